@@ -1,0 +1,373 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself (numpy, moment equations, closed forms, brute force, an independent
+high-precision algorithm, or values printed in the paper)."""
+import itertools
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs as si
+import closed_forms
+import dp_pin
+
+CC, GL, TRAP = si.RULE_CLENSHAW_CURTIS, si.RULE_GAUSS_LEGENDRE, si.RULE_TRAPEZOID
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _n(kind, level):
+    if kind == GL:
+        return level
+    return 1 if level == 1 else 2 ** (level - 1) + 1
+
+
+# --------------------------------------------------------------------------
+# 1-D rules (Eqs. 2.10, 2.11, 2.13)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [CC, GL, TRAP])
+def test_rule_weights_sum_to_length(kind):
+    for level in range(1, 10):
+        x, w = oracle.rule(kind, level)
+        assert len(x) == _n(kind, level)
+        assert abs(w.sum() - 1.0) < 1e-14
+        assert np.all(np.diff(x) > 0) and x[0] >= 0 and x[-1] <= 1
+
+
+def test_gl_nodes_match_numpy_leggauss():
+    for n in range(1, 14):
+        x, w = oracle.rule(GL, n)
+        xr, wr = np.polynomial.legendre.leggauss(n)
+        np.testing.assert_allclose(x, (xr + 1) / 2, rtol=0, atol=2e-15)
+        np.testing.assert_allclose(w, wr / 2, rtol=0, atol=2e-15)
+
+
+def _moment_error(x, w, p):
+    return abs(np.dot(w, x ** p) - 1.0 / (p + 1))
+
+
+def test_gl_exactness_degree():
+    # n Gauss points integrate degree 2n-1 exactly and not degree 2n
+    for n in range(1, 12):
+        x, w = oracle.rule(GL, n)
+        for p in range(2 * n):
+            assert _moment_error(x, w, p) < 1e-14
+        if n <= 8:
+            assert _moment_error(x, w, 2 * n) > 1e-12
+
+
+def test_cc_nodes_are_chebyshev_extrema():
+    for level in range(2, 9):
+        x, _ = oracle.rule(CC, level)
+        ref = np.sort((np.polynomial.chebyshev.chebpts2(len(x)) + 1) / 2)
+        np.testing.assert_allclose(x, ref, rtol=0, atol=2e-16)
+
+
+def test_cc_weights_solve_moment_equations():
+    # the interpolatory weights on the CC nodes are fixed by exactness for
+    # 1, x, ..., x^(n-1); solve that system in numpy (Chebyshev basis for
+    # conditioning) and compare with the explicit formula of Eq. 2.11
+    for level in range(2, 8):
+        x, w = oracle.rule(CC, level)
+        t = 2 * x - 1
+        n = len(x)
+        V = np.polynomial.chebyshev.chebvander(t, n - 1).T
+        m = np.array([0.0 if k % 2 else 2.0 / (1 - k * k) for k in range(n)]) / 2
+        wr = np.linalg.solve(V, m)
+        np.testing.assert_allclose(w, wr, rtol=0, atol=1e-14)
+
+
+def test_cc_level2_is_simpson():
+    x, w = oracle.rule(CC, 2)
+    np.testing.assert_allclose(x, [0, 0.5, 1], atol=0)
+    np.testing.assert_allclose(w, [1 / 6, 2 / 3, 1 / 6], rtol=1e-15)
+
+
+def test_cc_exactness_degree():
+    # n (odd) CC points integrate degree n exactly, not degree n+1
+    for level in range(2, 8):
+        x, w = oracle.rule(CC, level)
+        n = len(x)
+        for p in range(n + 1):
+            assert _moment_error(x, w, p) < 1e-14
+        if n <= 9:
+            assert _moment_error(x, w, n + 1) > 1e-12
+
+
+def test_trapezoid_rule():
+    for level in range(2, 8):
+        x, w = oracle.rule(TRAP, level)
+        n = len(x)
+        np.testing.assert_allclose(x, np.linspace(0, 1, n), atol=1e-16)
+        h = 1.0 / (n - 1)
+        ref = np.full(n, h)
+        ref[0] = ref[-1] = h / 2
+        np.testing.assert_allclose(w, ref, rtol=1e-15)
+        assert _moment_error(x, w, 1) < 1e-15  # exact for linears
+        # O(h^2) error on x^2
+        assert abs(_moment_error(x, w, 2) - h * h / 6) < 1e-14
+
+
+@pytest.mark.parametrize("kind", [CC, TRAP])
+def test_nested_rules_share_nodes_exactly(kind):
+    for level in range(2, 9):
+        x1, _ = oracle.rule(kind, level)
+        x0, _ = oracle.rule(kind, level - 1)
+        assert set(x0.tolist()) <= set(x1.tolist())
+
+
+@pytest.mark.parametrize("kind", [CC, GL, TRAP])
+def test_delta_rule_is_difference_of_rules(kind):
+    rng = np.random.default_rng(0)
+    for level in range(2, 8):
+        xd, wd = oracle.delta_rule(kind, level)
+        x1, w1 = oracle.rule(kind, level)
+        x0, w0 = oracle.rule(kind, level - 1)
+        assert abs(wd.sum()) < 1e-14
+        expected_n = len(x1) if kind != GL else len(x1) + len(x0)
+        assert len(xd) == expected_n
+        for _ in range(3):
+            c = rng.standard_normal(8)
+            g = lambda t: np.polynomial.polynomial.polyval(np.cos(3 * t), c)
+            assert abs(np.dot(wd, g(xd)) - (np.dot(w1, g(x1)) - np.dot(w0, g(x0)))) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Sparse grid structure (Eqs. 2.6-2.9)
+# --------------------------------------------------------------------------
+
+CASES_SMALL = [(CC, 1, 4), (CC, 2, 3), (CC, 3, 3), (CC, 4, 2), (GL, 2, 4), (GL, 3, 3),
+               (TRAP, 3, 3), (GL, 5, 2)]
+
+
+@pytest.mark.parametrize("kind,d,L", CASES_SMALL)
+def test_weights_sum_to_volume(kind, d, L):
+    for form in (oracle.FORM_DIFF, oracle.FORM_COMB):
+        _, W = oracle.points(kind, d, L, form)
+        assert abs(W.sum() - 1.0) < 1e-12
+
+
+def _merge(X, W):
+    keys = {}
+    for x, w in zip(map(tuple, X), W):
+        keys[x] = keys.get(x, 0.0) + w
+    return keys
+
+
+def test_n_d_q_counts():
+    # n_d^q of Eq. 2.6 (points with repetition): dimension-by-dimension count
+    # against the enumerated comb-form point list, plus two closed forms
+    for kind, d, L in CASES_SMALL + [(CC, 6, 3), (GL, 4, 5)]:
+        X, _ = oracle.points(kind, d, L, oracle.FORM_COMB)
+        assert oracle.count_points(kind, d, L) == len(X)
+    for d in range(2, 40, 7):
+        # L = 1: centre (|k| = 0) plus d subgrids of 3 points
+        assert oracle.count_points(CC, d, 1) == 1 + 3 * d
+    for L in range(0, 10):
+        assert oracle.count_points(CC, 1, L) == _n(CC, L + 1)
+    # the workloads' denominators
+    assert oracle.count_points(CC, 4, 5) == 5257
+    assert oracle.count_points(GL, 12, 6) == 593775
+    assert oracle.count_points(CC, 100, 3) == 4560651
+    assert oracle.count_points(CC, 1000, 2) == 4503501
+
+
+def test_paper_distinct_node_counts():
+    path = os.path.join(GOLDEN, "paper_gl_node_counts.txt")
+    rows = [list(map(int, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
+    for d, N, count in rows:
+        X, W = oracle.points(GL, d, N - 1, oracle.FORM_COMB)
+        assert len(_merge(X, W)) == count, (d, N)
+
+
+def _monomials(d, deg):
+    for alpha in itertools.product(range(deg + 1), repeat=d):
+        if sum(alpha) == deg:
+            yield alpha
+
+
+@pytest.mark.parametrize("kind,d,L", [(CC, 3, 2), (CC, 3, 3), (CC, 4, 4), (CC, 2, 5),
+                                      (GL, 3, 2), (GL, 3, 3), (GL, 2, 5)])
+def test_polynomial_exactness(kind, d, L):
+    # Smolyak with 1-D rules exact to degree 2k+1 at excess k integrates every
+    # monomial of total degree <= 2L+1 exactly (Novak & Ritter 1996), and
+    # misses some monomial of degree 2L+2
+    for form in (oracle.FORM_DIFF, oracle.FORM_COMB):
+        X, W = oracle.points(kind, d, L, form)
+        for deg in range(2 * L + 2):
+            for alpha in _monomials(d, deg):
+                v = np.dot(W, np.prod(X ** np.array(alpha), axis=1))
+                ref = np.prod([1.0 / (a + 1) for a in alpha])
+                assert abs(v - ref) < 1e-13, (alpha, v, ref)
+        worst = max(abs(np.dot(W, np.prod(X ** np.array(al), axis=1)) -
+                        np.prod([1.0 / (a + 1) for a in al])) for al in _monomials(d, 2 * L + 2))
+        assert worst > 1e-8
+
+
+def test_full_tensor_differs_from_sparse():
+    # d = 2, L = 2 (CC): the full tensor rule J^3 x J^3 integrates x^4 y^4;
+    # the sparse rule does not, while both integrate x^3 y^2 exactly
+    X, W = oracle.points(CC, 2, 2, oracle.FORM_DIFF)
+    x3, w3 = oracle.rule(CC, 3)
+    TX = np.array(list(itertools.product(x3, x3)))
+    TW = np.array([a * b for a, b in itertools.product(w3, w3)])
+    for (p, q), both in (((3, 2), True), ((4, 4), False)):
+        ref = 1.0 / ((p + 1) * (q + 1))
+        tens = np.dot(TW, TX[:, 0] ** p * TX[:, 1] ** q)
+        sp = np.dot(W, X[:, 0] ** p * X[:, 1] ** q)
+        assert abs(tens - ref) < 1e-15
+        assert (abs(sp - ref) < 1e-15) == both
+
+
+def test_difference_form_points_are_combination_form_points():
+    # merged weights (Eq. 2.8): both forms define the same point measure
+    for kind, d, L in [(CC, 2, 3), (CC, 3, 3), (TRAP, 3, 2), (GL, 2, 3)]:
+        A = _merge(*oracle.points(kind, d, L, oracle.FORM_DIFF))
+        B = _merge(*oracle.points(kind, d, L, oracle.FORM_COMB))
+        for k in set(A) | set(B):
+            assert abs(A.get(k, 0.0) - B.get(k, 0.0)) < 1e-13
+
+
+def test_d1_is_the_1d_rule():
+    for kind in (CC, GL, TRAP):
+        for L in range(0, 7):
+            p = np.array([0.7, 0.3])
+            r = oracle.integrate(kind, si.FAM_GAUSSIAN, p, 1, L)
+            x, w = oracle.rule(kind, L + 1)
+            ref = np.dot(w, np.exp(-0.49 * (x - 0.3) ** 2))
+            assert abs(r.value - ref) < 1e-15 * max(1.0, r.cond)
+
+
+def test_brute_force_merged_points():
+    # Eq. 2.8: Q = sum_k w_k f(x^k) over the distinct points, f evaluated
+    # directly in numpy on the merged list
+    rng = np.random.default_rng(5)
+    for kind, d, L in [(CC, 2, 4), (CC, 3, 3), (GL, 3, 3), (TRAP, 2, 3)]:
+        a = rng.random(d)
+        u = rng.random(d)
+        merged = _merge(*oracle.points(kind, d, L, oracle.FORM_COMB))
+        X = np.array(list(merged.keys()))
+        W = np.array(list(merged.values()))
+        f = np.exp(-np.sum(a ** 2 * (X - u) ** 2, axis=1))
+        r = oracle.integrate(kind, si.FAM_GAUSSIAN, np.concatenate([a, u]), d, L)
+        assert abs(r.value - np.dot(W, f)) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Values: forms agree, independent DP pin, closed forms, the paper's tables
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fam", [0, 1, 2, 3, 4])
+def test_combination_form_equals_difference_form(fam):
+    for kind, d, L in [(CC, 3, 4), (GL, 4, 3), (TRAP, 3, 3), (CC, 6, 2)]:
+        p = si.item_params(fam, d, 100 + fam + d)
+        a = oracle.integrate(kind, fam, p, d, L, oracle.FORM_DIFF)
+        b = oracle.integrate(kind, fam, p, d, L, oracle.FORM_COMB)
+        assert a.exp2 == b.exp2 or abs(a.value - b.value) < 1e-14
+        rel = abs(np.ldexp(a.mant, a.exp2 - b.exp2) - b.mant) / abs(b.mant)
+        assert rel < 1e-15 * max(a.cond, b.cond) * 10
+
+
+def _dp_cases():
+    yield si.cfg1()
+    yield si.cfg2()
+    yield si.cfg3(si.FAM_PRODUCT_PEAK)
+    yield si.cfg3(si.FAM_GAUSSIAN)
+    yield si.cfg5()
+    for k, it in enumerate(si.batch(n=6, seed=99, d_hi=40, L_hi=4)):
+        yield dict(name="batch%d" % k, **it)
+
+
+@pytest.mark.parametrize("case", list(_dp_cases()), ids=lambda c: c["name"])
+def test_oracle_matches_separable_dp(case):
+    ref = dp_pin.smolyak_value(case["rule"], case["fam"], case["params"], case["d"], case["L"])
+    r = oracle.integrate(case["rule"], case["fam"], case["params"], case["d"], case["L"])
+    err = dp_pin.rel_err(r.mant, r.exp2, ref)
+    assert err < 3e-13, err
+
+
+def test_oracle_quadrature_error_vs_closed_forms():
+    # the rule converges to the integral at the expected order of magnitude
+    bounds = {"cfg1": 1e-11, "cfg2": 1e-10, "cfg3": 1e-5, "cfg5": 1e-3}
+    for c in [si.cfg1(), si.cfg2(), si.cfg3(2), si.cfg3(3), si.cfg5()]:
+        r = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
+        ex = closed_forms.exact(c["fam"], c["params"], c["d"])
+        err = float(abs(closed_forms.as_mp(r.mant, r.exp2) - ex) / abs(ex))
+        assert err < bounds[c["name"][:4]], (c["name"], err)
+
+
+def test_paper_tables_5_6_to_5_8():
+    path = os.path.join(GOLDEN, "paper_gl_tables.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        _, fam, d, N, printed = line.split()
+        d, N, printed = int(d), int(N), float(printed)
+        # map [-1,1]^d to [0,1]^d by x = 2y - 1 (the relative error is unchanged)
+        if fam == "exp":
+            f, a, u = 0, np.array([2.0 * (-1) ** i for i in range(d)]), np.zeros(d)
+        elif fam == "cos":
+            f, a, u = 1, np.full(d, 2.0), np.zeros(d)
+            u[0] = 1.0 - d / (2 * math.pi)
+        else:
+            f, a, u = 2, np.full(d, 1 / 0.45), np.full(d, 0.8)
+        p = np.concatenate([a, u])
+        r = oracle.integrate(GL, f, p, d, N - 1)
+        ex = closed_forms.exact(f, p, d)
+        err = float(abs(closed_forms.as_mp(r.mant, r.exp2) - ex) / abs(ex))
+        assert abs(err / printed - 1) < 2e-4, (fam, d, N, err, printed)
+
+
+def test_thread_count_does_not_change_result():
+    c = si.cfg3(si.FAM_GAUSSIAN)
+    a = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"], nthreads=1)
+    b = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"], nthreads=7)
+    assert a.mant == b.mant and a.exp2 == b.exp2
+
+
+def test_product_peak_scale_underflow():
+    # d = 200 product peak: the value is far below the smallest double, the
+    # mantissa/exponent pair still matches the DP pin
+    p = si.item_params(si.FAM_PRODUCT_PEAK, 200, 1234)
+    r = oracle.integrate(CC, 2, p, 200, 2)
+    assert r.value == 0.0 and r.exp2 < -1100
+    ref = dp_pin.smolyak_value(CC, 2, p, 200, 2)
+    assert dp_pin.rel_err(r.mant, r.exp2, ref) < 3e-13
+
+
+# --------------------------------------------------------------------------
+# Gradient
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fam", [0, 1, 2, 3, 4])
+def test_gradient_matches_dp_and_finite_differences(fam):
+    kind, d, L = (GL, 7, 3) if fam % 2 else (CC, 9, 3)
+    p = si.item_params(fam, d, 77 + fam)
+    idx = list(range(2 * d))
+    r, g = oracle.gradient(kind, fam, p, d, L, idx)
+    g = np.ldexp(g, r.exp2)
+    ref = np.array([float(v) for v in dp_pin.smolyak_gradient(kind, fam, p, d, L, idx)])
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+    # central differences on a few coordinates
+    for j in (0, d - 1, d, 2 * d - 1):
+        h = 1e-5 * max(abs(p[j]), 1e-3)
+        pp, pm = p.copy(), p.copy()
+        pp[j] += h
+        pm[j] -= h
+        fp = oracle.integrate(kind, fam, pp, d, L).value
+        fm = oracle.integrate(kind, fam, pm, d, L).value
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-6 * max(np.abs(g).max(), 1e-300)
+
+
+def test_gradient_cfg5_subset_matches_dp():
+    c = si.cfg5()
+    idx = dp_pin.sample_idx(c["d"])
+    r, g = oracle.gradient(c["rule"], c["fam"], c["params"], c["d"], c["L"], idx)
+    ref = np.array([float(v) for v in
+                    dp_pin.smolyak_gradient(c["rule"], c["fam"], c["params"], c["d"], c["L"], idx)])
+    g = np.ldexp(g, r.exp2)
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
