@@ -1,0 +1,266 @@
+/*
+ * sg.h - C ABI of libsg: Smolyak sparse-grid quadrature on one GB300 GPU,
+ * evaluated by multilevel dimension iteration (MDI).
+ *
+ * What the library computes (Zhong & Feng, "An efficient and fast sparse grid
+ * algorithm for high-dimensional numerical integration", Section 2.1):
+ *
+ *   Q_d^q f = sum_{q-d+1 <= |l| <= q} (-1)^{q-|l|} C(d-1, q-|l|)
+ *             sum_{|l| fixed} (J^{l_1} x ... x J^{l_d}) f               (Eq. 2.6)
+ *
+ * on the unit cube [0,1]^d, with J^l the level-l 1-D rule (Eqs. 2.10, 2.11,
+ * 2.13, mapped from [-1,1] to [0,1]).  q = d + L; L = q - d >= 0 is the
+ * "excess level".  The GPU evaluates the equal coordinate-wise form (Eq. 2.9,
+ * read as a sum of tensor products of difference rules J^l - J^{l-1}) with
+ * the direction-by-direction folding of Algorithms 3.1-3.3: the grid is never
+ * stored, and partial sums over the leading directions of a cluster of points
+ * are reused for every point of the cluster.
+ *
+ * Integrands are the Genz-type families of the paper's Section 4 and 5
+ * tests.  Parameters are always 2d doubles, params = [a_0..a_{d-1},
+ * u_0..u_{d-1}]:
+ *   SG_FAM_EXP_LINEAR    f = exp(sum a_i x_i)                       (a)
+ *   SG_FAM_OSCILLATORY   f = cos(2 pi u_0 + sum a_i x_i)            (a, u_0)
+ *   SG_FAM_PRODUCT_PEAK  f = prod 1 / (a_i^-2 + (x_i - u_i)^2)      (a, u)
+ *   SG_FAM_GAUSSIAN      f = exp(-sum a_i^2 (x_i - u_i)^2)          (a, u)
+ *   SG_FAM_GAUSSIAN_LIN  f = exp(-sum a_i (x_i - u_i)^2)            (a, u)
+ * Unused entries are ignored (their gradient is 0).
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned; nothing throws across the ABI.  On error the
+ *    outputs are left untouched.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream) of the
+ *    current device.  Host-result entry points synchronise that stream
+ *    before returning; sg_integrate_async does not.
+ *  - The library owns rule handles and its internal device scratch (cached
+ *    per device and grown on demand, freed at process exit).  The caller
+ *    owns every params / result buffer it passes.
+ *  - Calls from different host threads must use different streams.
+ *  - Results are Q = mant * 2^exp2 (the product-peak value underflows a
+ *    double for d >~ 150); `value` holds ldexp(mant, exp2).
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SG_API __attribute__((visibility("default")))
+#else
+#define SG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,       /* NULL pointer, bad enum, d < 1, q < d, ... */
+    SG_ERANGE = 2,       /* size beyond a documented limit */
+    SG_ENOMEM = 3,       /* device or host allocation failed */
+    SG_ECUDA = 4,        /* a CUDA runtime call failed */
+    SG_ETIMEOUT = 5,     /* reserved: no kernel of this library waits on another */
+    SG_EUNSUPPORTED = 6  /* combination not implemented (e.g. gradient of comb form) */
+} sg_status;
+
+/* 1-D rules; the numbering is the paper's r (Section 3.1). */
+typedef enum {
+    SG_RULE_TRAPEZOID = 1,        /* Eq. 2.10; level 1 = midpoint (reading of the paper) */
+    SG_RULE_CLENSHAW_CURTIS = 2,  /* Eq. 2.11; n_1 = 1, n_l = 2^(l-1) + 1, nested */
+    SG_RULE_GAUSS_LEGENDRE = 4    /* Eq. 2.13; n_l = l, not nested */
+} sg_rule_kind;
+
+typedef enum {
+    SG_FAM_EXP_LINEAR = 0,
+    SG_FAM_OSCILLATORY = 1,
+    SG_FAM_PRODUCT_PEAK = 2,
+    SG_FAM_GAUSSIAN = 3,
+    SG_FAM_GAUSSIAN_LIN = 4
+} sg_family;
+
+typedef enum {
+    SG_PREC_FP64 = 0,   /* every step in IEEE double */
+    SG_PREC_MIXED = 1   /* integrand evaluation and per-cluster folds in float;
+                           cross-cluster and cross-chunk sums in double with
+                           Neumaier compensation */
+} sg_precision;
+
+/* Which algebraic form of the same Smolyak sum the kernels enumerate.  All
+ * three give Q_d^q f up to rounding. */
+typedef enum {
+    SG_FORM_AUTO = 0,        /* SG_FORM_TELESCOPED */
+    SG_FORM_DIFFERENCE = 1,  /* sum_{|k|<=L} of tensor products of difference rules (Eq. 2.9) */
+    SG_FORM_TELESCOPED = 2,  /* difference rules in all but the last active direction;
+                                the last direction folds J^{M+1} - J^1 at once (Alg. 3.1) */
+    SG_FORM_COMBINATION = 3  /* Eq. 2.6 literally (binomial coefficients) */
+} sg_form;
+
+typedef struct sg_rule_s *sg_rule;  /* opaque, library-owned */
+
+typedef struct {
+    double value;      /* ldexp(mant, exp2); 0 or inf when out of double range */
+    double mant;       /* 0.5 <= |mant| < 1 (or 0) */
+    int64_t exp2;
+    double cond;       /* sum_p |W_p D_p| / |sum|: conditioning of the signed sum */
+    double err_est;    /* estimated relative rounding error of the result */
+    uint64_t points;   /* n_d^q: points of Eq. 2.6 with repetition (the metric's unit) */
+    uint64_t evals;    /* integrand deviations the kernels evaluated */
+    double seconds;    /* device time of the call (CUDA events) */
+} sg_result;
+
+/* Device-side result record written by sg_integrate_async (7 doubles). */
+typedef struct {
+    double mant;
+    double exp2;       /* integer-valued */
+    double value;
+    double cond;
+    double err_est;
+    double sum;        /* base + T before scaling (diagnostic) */
+    double abs_sum;    /* sum |W_p D_p| (diagnostic) */
+} sg_dev_result;
+
+/*
+ * Builds the 1-D rule tables of Eqs. 2.10, 2.11 or 2.13 on [0,1] for levels
+ * 1..max_level (host and device copies on the current device).  The
+ * handle may be used with any d and q with q - d + 1 <= max_level.
+ * Limits: 1 <= max_level <= 13 (4097 nodes for the nested rules).
+ * Errors: SG_EINVAL (bad kind, NULL out), SG_ERANGE (max_level), SG_ENOMEM,
+ * SG_ECUDA.
+ */
+SG_API sg_status sg_rule_init(sg_rule_kind kind, int max_level, sg_rule *out);
+
+/* Frees a handle from sg_rule_init.  NULL is accepted. */
+SG_API sg_status sg_rule_destroy(sg_rule rule);
+
+/*
+ * Copies the level-`level` rule on [0,1] (nodes ascending) into caller-owned
+ * host arrays x, w of capacity *n; on return *n = node count.  With x or w
+ * NULL only *n is set.  Errors: SG_EINVAL, SG_ERANGE (level, capacity).
+ */
+SG_API sg_status sg_rule_nodes(sg_rule rule, int level, double *x, double *w, int *n);
+
+/*
+ * n_d^q = sum over the multi-indices of Eq. 2.6 of prod_i n_{l_i}: the point
+ * count with repetition, the unit of the points/s metric.  Also the number
+ * of integrand deviations the kernels evaluate for `form` (evals may be
+ * NULL).  Errors: SG_EINVAL, SG_ERANGE (count beyond 2^64).
+ */
+SG_API sg_status sg_count_points(sg_rule rule, int d, int q, sg_form form, uint64_t *points,
+                          uint64_t *evals);
+
+/*
+ * One integral Q_d^q f.  params: 2d doubles, host memory (params_on_device
+ * = 0) or device memory of the current device (1).  Blocking: the result is
+ * valid on return.  Limits: 1 <= d <= 8192, 0 <= q - d <= max_level - 1,
+ * q - d <= 12, and the subgrid count must fit in 64 bits.
+ * Errors: SG_EINVAL, SG_ERANGE, SG_ENOMEM, SG_ECUDA.
+ */
+SG_API sg_status sg_integrate(sg_rule rule, sg_family fam, const double *params, int params_on_device,
+                       int d, int q, sg_precision prec, sg_form form, void *stream,
+                       sg_result *out);
+
+/*
+ * Asynchronous variant: params and the result live in device memory of the
+ * current device; every step is enqueued on `stream` and nothing
+ * synchronises.  The first call for a (rule, d, q, prec, form) builds and
+ * uploads that plan (host work plus a synchronous copy): do it once before
+ * timing or capturing.  Same limits and errors as sg_integrate.
+ */
+SG_API sg_status sg_integrate_async(sg_rule rule, sg_family fam, const double *d_params, int d, int q,
+                             sg_precision prec, sg_form form, void *stream,
+                             sg_dev_result *d_out);
+
+/* One batch entry: rule, family, dimension, q, and the offset of its 2d
+ * parameters in the shared parameter pool. */
+typedef struct {
+    sg_rule rule;
+    sg_family fam;
+    int d;
+    int q;
+    uint64_t param_offset;
+} sg_item;
+
+/*
+ * A batch of n integrals of uneven d and level, run by one persistent
+ * work-stealing launch (plus a table-setup launch), replayed from a CUDA graph
+ * cached for this batch layout.  params_pool: host (params_on_device = 0) or
+ * device memory; item k reads pool[param_offset .. param_offset + 2d).
+ * With prec = SG_PREC_MIXED and guard_tol > 0, items whose estimated
+ * rounding error exceeds guard_tol are recomputed in FP64 by a second
+ * persistent launch in the same graph.  out: n host records.  Blocking.
+ * Limits: 1 <= n <= 65536, per item as sg_integrate.
+ */
+SG_API sg_status sg_integrate_batch(const sg_item *items, int n, const double *params_pool,
+                             int params_on_device, sg_precision prec, double guard_tol,
+                             void *stream, sg_result *out);
+
+/*
+ * Value and gradient: dparams[j] = dQ / dparams[j] for all 2d parameters,
+ * written to caller-owned host (dparams_on_device = 0) or device memory.
+ * Computed by a hand-written adjoint kernel: for each direction i, the sum
+ * over every point where direction i is active of W_p f(x_p) times the
+ * partial derivative factor of direction i, with the other directions folded
+ * as in the forward pass; the centre term of each direction comes from Q.
+ * Supported with SG_FORM_DIFFERENCE / SG_FORM_TELESCOPED / AUTO; the
+ * combination form gives SG_EUNSUPPORTED.  Blocking.
+ */
+SG_API sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double *params,
+                            int params_on_device, int d, int q, sg_precision prec, void *stream,
+                            sg_result *out, double *dparams, int dparams_on_device);
+
+/* Static description of a status code. */
+SG_API const char *sg_status_string(sg_status s);
+
+/* Tuning knobs used by the launches (read by the autotuner; see
+ * sg_autotune).  points_per_chunk: target integrand evaluations per
+ * work-stealing chunk; ctas_per_sm: resident CTAs per SM of the persistent
+ * grid; warps_per_cta: warps per CTA. */
+typedef struct {
+    int points_per_chunk;
+    int ctas_per_sm;
+    int warps_per_cta;
+} sg_tuning;
+
+/* Reads / sets the tuning used for precision `prec` (process-wide). */
+SG_API sg_status sg_get_tuning(sg_precision prec, sg_tuning *t);
+SG_API sg_status sg_set_tuning(sg_precision prec, const sg_tuning *t);
+
+/*
+ * Times the given batch (as sg_integrate_batch would run it, without the
+ * guard) under each candidate of a built-in grid of (points_per_chunk,
+ * ctas_per_sm, warps_per_cta), keeps the fastest for `prec` and returns it
+ * in *best (and its median time in *best_ms).  Blocking; runs each candidate
+ * `reps` times.  Errors as sg_integrate_batch.
+ */
+SG_API sg_status sg_autotune(const sg_item *items, int n, const double *params_pool,
+                      int params_on_device, sg_precision prec, int reps, void *stream,
+                      sg_tuning *best, double *best_ms);
+
+
+/*
+ * Measurement hooks (no counterpart in the paper).  sg_profile_begin starts
+ * recording CUDA events around every fold-kernel launch this library
+ * enqueues on `stream` (not inside graph replays); sg_profile_end
+ * synchronises the stream, returns the summed device time of those launches
+ * in ms and their count, and stops recording.  Errors: SG_EINVAL, SG_ECUDA.
+ */
+SG_API sg_status sg_profile_begin(void *stream);
+SG_API sg_status sg_profile_end(void *stream, double *fold_ms, int *launches);
+
+/*
+ * Throughput ceiling of the fold's per-point work on this GPU: the same
+ * sequence as the fold's inner loop (argument add, weight product,
+ * deviation, weighted accumulate; in `prec`) on register-resident data, on
+ * a full grid of the device, without loads, enumeration or reduction.
+ * kind 0: expm1 deviation, 1: oscillatory deviation (points/s), 2: plain
+ * fused multiply-add chains (FLOP/s).  Blocking.  Errors: SG_EINVAL,
+ * SG_ECUDA.
+ */
+SG_API sg_status sg_ceiling(sg_precision prec, int kind, void *stream, double *rate);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

@@ -1,0 +1,893 @@
+// Host side of libsg: the C ABI of include/sg.h, the planner that turns an
+// integral into items / patterns / chunks, per-stream device workspaces and
+// the launch sequence (setup -> prep -> fold [-> guard pass] [-> adjoint]).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sg.h"
+#include "sg_kernels.h"
+#include "sg_plan.h"
+#include "sg_rules.h"
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return SG_ECUDA;    \
+    } while (0)
+
+
+// ---------------------------------------------------------------------------
+// status strings
+// ---------------------------------------------------------------------------
+
+extern "C" const char *sg_status_string(sg_status s) {
+    switch (s) {
+    case SG_OK: return "ok";
+    case SG_EINVAL: return "invalid argument";
+    case SG_ERANGE: return "size beyond a supported limit";
+    case SG_ENOMEM: return "out of memory";
+    case SG_ECUDA: return "CUDA runtime error";
+    case SG_ETIMEOUT: return "timeout";
+    case SG_EUNSUPPORTED: return "unsupported combination";
+    }
+    return "unknown status";
+}
+
+static std::mutex g_mu;
+
+// ---------------------------------------------------------------------------
+// per-device context: SM count and the binomial table
+// ---------------------------------------------------------------------------
+
+struct DevCtx {
+    int sms = 0;
+    u64 *binom = nullptr;
+};
+static std::map<int, DevCtx> g_dev;
+
+static sg_status dev_ctx(DevCtx **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    auto it = g_dev.find(dev);
+    if (it != g_dev.end()) {
+        *out = &it->second;
+        return SG_OK;
+    }
+    DevCtx c;
+    CK(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+    std::vector<u64> B((size_t)SG_BINOM_K * (SG_MAX_D + 1));
+    sg_fill_binomials(B.data());
+    if (cudaMalloc(&c.binom, B.size() * sizeof(u64)) != cudaSuccess) return SG_ENOMEM;
+    CK(cudaMemcpy(c.binom, B.data(), B.size() * sizeof(u64), cudaMemcpyHostToDevice));
+    g_dev[dev] = c;
+    *out = &g_dev[dev];
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rules
+// ---------------------------------------------------------------------------
+
+extern "C" sg_status sg_rule_init(sg_rule_kind kind, int max_level, sg_rule *out) {
+    if (!out || (kind != SG_RULE_TRAPEZOID && kind != SG_RULE_CLENSHAW_CURTIS &&
+                 kind != SG_RULE_GAUSS_LEGENDRE))
+        return SG_EINVAL;
+    if (max_level < 1 || max_level > SG_MAX_LEVEL) return SG_ERANGE;
+    sg_rule_s *r = new sg_rule_s();
+    r->kind = kind;
+    r->max_level = max_level;
+    if (cudaGetDevice(&r->device) != cudaSuccess) {
+        delete r;
+        return SG_ECUDA;
+    }
+    std::vector<double> tx(2 * 4097 + 2), tw(2 * 4097 + 2);
+    std::vector<double2> all;
+    for (int bk = 0; bk < 3; bk++)
+        for (int k = 1; k < max_level; k++) {
+            int n = sg_block(kind, bk, k, tx.data(), tw.data());
+            r->x[bk][k].assign(tx.begin(), tx.begin() + n);
+            r->w[bk][k].assign(tw.begin(), tw.begin() + n);
+            r->off[bk][k] = (int)all.size();
+            for (int j = 0; j < n; j++) all.push_back(make_double2(tx[j], tw[j]));
+        }
+    if (all.empty()) all.push_back(make_double2(0.5, 1.0));
+    if (cudaMalloc(&r->d_xw, all.size() * sizeof(double2)) != cudaSuccess) {
+        delete r;
+        return SG_ENOMEM;
+    }
+    if (cudaMemcpy(r->d_xw, all.data(), all.size() * sizeof(double2), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+        cudaFree(r->d_xw);
+        delete r;
+        return SG_ECUDA;
+    }
+    *out = r;
+    return SG_OK;
+}
+
+static void plans_drop_rule(sg_rule r);
+
+extern "C" sg_status sg_rule_destroy(sg_rule r) {
+    if (!r) return SG_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        plans_drop_rule(r);
+    }
+    cudaFree(r->d_xw);
+    delete r;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_rule_nodes(sg_rule r, int level, double *x, double *w, int *n) {
+    if (!r || !n) return SG_EINVAL;
+    if (level < 1 || level > r->max_level) return SG_ERANGE;
+    int m = sg_level_nodes(r->kind, level);
+    if (x && w) {
+        if (*n < m) return SG_ERANGE;
+        sg_rule_level(r->kind, level, x, w);
+    }
+    *n = m;
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tuning
+// ---------------------------------------------------------------------------
+
+// index 0: FP64, 1: mixed
+static sg_tuning g_tune[2] = {{2048, 8, 8}, {16384, 8, 8}};
+
+extern "C" sg_status sg_get_tuning(sg_precision prec, sg_tuning *t) {
+    if (!t || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED)) return SG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    *t = g_tune[prec];
+    return SG_OK;
+}
+
+extern "C" sg_status sg_set_tuning(sg_precision prec, const sg_tuning *t) {
+    if (!t || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED)) return SG_EINVAL;
+    if (t->points_per_chunk < 32 || t->points_per_chunk > (1 << 26) || t->ctas_per_sm < 1 ||
+        t->ctas_per_sm > 32 || t->warps_per_cta < 1 || t->warps_per_cta > 32)
+        return SG_ERANGE;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune[prec] = *t;
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// plans on the device
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static size_t carve(size_t &cur, size_t n) {
+    size_t off = (cur + 255) & ~(size_t)255;
+    cur = off + n * sizeof(T);
+    return off;
+}
+
+static void plan_free(Plan *P) {
+    if (P->dmem) cudaFree(P->dmem);
+    plan_free_host(P);
+}
+
+// Resolves the rule-block pointers and copies a host plan to the device.
+static sg_status plan_upload(Plan *P) {
+    cudaGetDevice(&P->device);
+    // device copy, one allocation
+    size_t sz = 0;
+    const size_t o_int = carve<SgIntegralDev>(sz, P->integrals.size());
+    const size_t o_blk = carve<SgBlockDev>(sz, P->blocks.size());
+    const size_t o_be = carve<long long>(sz, P->block_end.size());
+    const size_t o_it = carve<SgItemDev>(sz, P->items.size());
+    const size_t o_ro = carve<SgItemRole>(sz, P->roles.size());
+    const size_t o_ii = carve<int>(sz, P->item_integral.size());
+    const size_t o_pa = carve<SgPatDev>(sz, P->pats.size());
+    const size_t o_pc = carve<u64>(sz, P->pat_chunk0.size());
+    const size_t o_do = carve<int>(sz, P->delta_off.size() + 1);
+    const size_t o_dm = carve<int>(sz, P->delta_m.size() + 1);
+    std::vector<unsigned char> host(sz, 0);
+    memcpy(&host[o_int], P->integrals.data(), P->integrals.size() * sizeof(SgIntegralDev));
+    memcpy(&host[o_blk], P->blocks.data(), P->blocks.size() * sizeof(SgBlockDev));
+    memcpy(&host[o_be], P->block_end.data(), P->block_end.size() * sizeof(long long));
+    memcpy(&host[o_it], P->items.data(), P->items.size() * sizeof(SgItemDev));
+    memcpy(&host[o_ro], P->roles.data(), P->roles.size() * sizeof(SgItemRole));
+    memcpy(&host[o_ii], P->item_integral.data(), P->item_integral.size() * sizeof(int));
+    memcpy(&host[o_pa], P->pats.data(), P->pats.size() * sizeof(SgPatDev));
+    memcpy(&host[o_pc], P->pat_chunk0.data(), P->pat_chunk0.size() * sizeof(u64));
+    if (!P->delta_off.empty()) {
+        memcpy(&host[o_do], P->delta_off.data(), P->delta_off.size() * sizeof(int));
+        memcpy(&host[o_dm], P->delta_m.data(), P->delta_m.size() * sizeof(int));
+    }
+    if (cudaMalloc(&P->dmem, sz) != cudaSuccess) {
+        P->dmem = nullptr;
+        return SG_ENOMEM;
+    }
+    if (cudaMemcpy(P->dmem, host.data(), sz, cudaMemcpyHostToDevice) != cudaSuccess) return SG_ECUDA;
+    unsigned char *b = (unsigned char *)P->dmem;
+    P->d_integrals = (SgIntegralDev *)(b + o_int);
+    P->d_blocks = (SgBlockDev *)(b + o_blk);
+    P->d_block_end = (long long *)(b + o_be);
+    P->d_items = (SgItemDev *)(b + o_it);
+    P->d_roles = (SgItemRole *)(b + o_ro);
+    P->d_item_integral = (int *)(b + o_ii);
+    P->d_pats = (SgPatDev *)(b + o_pa);
+    P->d_pat_chunk0 = (u64 *)(b + o_pc);
+    P->d_delta_off = (int *)(b + o_do);
+    P->d_delta_m = (int *)(b + o_dm);
+    P->d_delta_xw = P->reqs[0].rule->d_xw;
+    return SG_OK;
+}
+
+static sg_status build_plan(const std::vector<Req> &reqs, int prec, const sg_tuning &tune, int sms,
+                            Plan **out) {
+    Plan *P = nullptr;
+    sg_status st = build_plan_host(reqs, prec, tune, sms, &P);
+    if (st != SG_OK) return st;
+    st = plan_upload(P);
+    if (st != SG_OK) {
+        plan_free(P);
+        return st;
+    }
+    *out = P;
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan cache
+// ---------------------------------------------------------------------------
+
+struct PlanKey {
+    std::vector<Req> reqs;
+    int prec;
+    sg_tuning t;
+    int device;
+    bool operator<(const PlanKey &o) const {
+        if (device != o.device) return device < o.device;
+        if (prec != o.prec) return prec < o.prec;
+        if (t.points_per_chunk != o.t.points_per_chunk) return t.points_per_chunk < o.t.points_per_chunk;
+        if (t.ctas_per_sm != o.t.ctas_per_sm) return t.ctas_per_sm < o.t.ctas_per_sm;
+        if (t.warps_per_cta != o.t.warps_per_cta) return t.warps_per_cta < o.t.warps_per_cta;
+        if (reqs.size() != o.reqs.size()) return reqs.size() < o.reqs.size();
+        for (size_t i = 0; i < reqs.size(); i++) {
+            const Req &a = reqs[i], &b = o.reqs[i];
+            auto ta = std::make_tuple(a.rule, a.fam, a.d, a.L, a.form, a.param_off, a.grad);
+            auto tb = std::make_tuple(b.rule, b.fam, b.d, b.L, b.form, b.param_off, b.grad);
+            if (ta != tb) return ta < tb;
+        }
+        return false;
+    }
+};
+static std::map<PlanKey, Plan *> g_plans;
+
+static void plans_drop_rule(sg_rule r) {
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        bool uses = false;
+        for (auto &q : it->first.reqs) uses |= q.rule == r;
+        if (uses) {
+            cudaDeviceSynchronize();
+            plan_free(it->second);
+            it = g_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Requires g_mu held.
+static sg_status get_plan(const std::vector<Req> &reqs, int prec, Plan **out) {
+    DevCtx *C = nullptr;
+    sg_status st = dev_ctx(&C);
+    if (st != SG_OK) return st;
+    PlanKey k;
+    k.reqs = reqs;
+    k.prec = prec;
+    k.t = g_tune[prec];
+    cudaGetDevice(&k.device);
+    auto it = g_plans.find(k);
+    if (it != g_plans.end()) {
+        *out = it->second;
+        return SG_OK;
+    }
+    Plan *P = nullptr;
+    st = build_plan(reqs, prec, k.t, C->sms, &P);
+    if (st != SG_OK) return st;
+    if (g_plans.size() > 256) {  // bound the cache
+        cudaDeviceSynchronize();
+        for (auto &kv : g_plans) plan_free(kv.second);
+        g_plans.clear();
+    }
+    g_plans[k] = P;
+    *out = P;
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-stream workspaces
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct GraphEntry {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+};
+
+struct Workspace {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf tab32, tab64, slots, counters, flags, bases, vars, out, vout, grad, params;
+    void *h_pinned = nullptr;
+    size_t h_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    unsigned epoch = 0;
+    std::map<std::tuple<const Plan *, const double *, double, unsigned>, GraphEntry> graphs;
+    // fold-kernel timing (sg_profile_begin / sg_profile_end)
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
+    size_t prof_used = 0;
+};
+
+// Records an event pair around a fold launch when profiling is on.
+static cudaError_t prof_mark(Workspace *W, bool start) {
+    if (!W->profiling) return cudaSuccess;
+    if (start) {
+        if (W->prof_used == W->prof.size()) {
+            std::pair<cudaEvent_t, cudaEvent_t> ev;
+            cudaError_t e = cudaEventCreate(&ev.first);
+            if (e == cudaSuccess) e = cudaEventCreate(&ev.second);
+            if (e != cudaSuccess) return e;
+            W->prof.push_back(ev);
+        }
+        return cudaEventRecord(W->prof[W->prof_used].first, W->stream);
+    }
+    return cudaEventRecord(W->prof[W->prof_used++].second, W->stream);
+}
+static std::map<std::pair<int, cudaStream_t>, Workspace *> g_ws;
+
+static void drop_graphs(Workspace *W) {
+    for (auto &kv : W->graphs) {
+        if (kv.second.x) cudaGraphExecDestroy(kv.second.x);
+        if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    }
+    W->graphs.clear();
+}
+
+static sg_status get_ws(cudaStream_t s, Workspace **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    auto key = std::make_pair(dev, s);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) {
+        *out = it->second;
+        return SG_OK;
+    }
+    Workspace *W = new Workspace();
+    W->device = dev;
+    W->stream = s;
+    if (cudaEventCreate(&W->ev0) != cudaSuccess || cudaEventCreate(&W->ev1) != cudaSuccess) {
+        delete W;
+        return SG_ECUDA;
+    }
+    g_ws[key] = W;
+    *out = W;
+    return SG_OK;
+}
+
+static sg_status ensure(Workspace *W, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.cap >= bytes) return SG_OK;
+    cudaStreamSynchronize(W->stream);
+    drop_graphs(W);
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    size_t cap = std::max(bytes, b.cap + b.cap / 2);
+    cap = (cap + 4095) & ~(size_t)4095;
+    if (cudaMalloc(&b.p, cap) != cudaSuccess) {
+        b.p = nullptr;
+        b.cap = 0;
+        cudaGetLastError();
+        return SG_ENOMEM;
+    }
+    b.cap = cap;
+    W->epoch++;
+    return SG_OK;
+}
+
+static sg_status ensure_host(Workspace *W, size_t bytes) {
+    if (W->h_pinned && W->h_cap >= bytes) return SG_OK;
+    cudaStreamSynchronize(W->stream);
+    if (W->h_pinned) cudaFreeHost(W->h_pinned);
+    W->h_pinned = nullptr;
+    size_t cap = std::max<size_t>(bytes, 4096);
+    if (cudaMallocHost(&W->h_pinned, cap) != cudaSuccess) {
+        W->h_pinned = nullptr;
+        W->h_cap = 0;
+        cudaGetLastError();
+        return SG_ENOMEM;
+    }
+    W->h_cap = cap;
+    return SG_OK;
+}
+
+#define ST(call)                         \
+    do {                                 \
+        sg_status s_ = (call);           \
+        if (s_ != SG_OK) return s_;      \
+    } while (0)
+
+// Makes every buffer a plan needs large enough (outside any capture).
+static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need64,
+                            size_t param_doubles) {
+    if (need32) ST(ensure(W, W->tab32, (size_t)P->nentries * sizeof(float2)));
+    if (need64) ST(ensure(W, W->tab64, (size_t)P->nentries * sizeof(double2)));
+    ST(ensure(W, W->slots, (size_t)P->nchunks * sizeof(SgSlot)));
+    ST(ensure(W, W->counters, 16 + 4 * P->items.size()));
+    ST(ensure(W, W->flags, 4 * P->items.size()));
+    ST(ensure(W, W->bases, P->integrals.size() * sizeof(SgBaseDev)));
+    ST(ensure(W, W->vars, P->items.size() * sizeof(SgItemVar)));
+    ST(ensure(W, W->out, (size_t)P->nout * sizeof(SgOutDev)));
+    ST(ensure(W, W->vout, (size_t)std::max<long long>(P->nv, 1) * sizeof(double)));
+    ST(ensure(W, W->grad, (size_t)2 * std::max(P->max_d, 1) * sizeof(double)));
+    if (param_doubles) ST(ensure(W, W->params, param_doubles * sizeof(double)));
+    return SG_OK;
+}
+
+static SgLaunchCfg fold_cfg(const Plan *P, int prec, int sms) {
+    SgLaunchCfg c;
+    c.warps_per_cta = P->tune.warps_per_cta;
+    int occ = sg_fold_occupancy(prec, 0, c.warps_per_cta);
+    int per_sm = std::max(1, std::min(occ, P->tune.ctas_per_sm));
+    long long ctas = (long long)sms * per_sm;
+    const long long need = (long long)((P->nchunks + c.warps_per_cta - 1) / c.warps_per_cta);
+    if (need < ctas) ctas = std::max<long long>(need, 1);
+    c.ctas = (int)ctas;
+    return c;
+}
+
+// Enqueues the whole computation of a plan on W->stream (capturable: no
+// allocation, no synchronisation).  prec_run: 0 FP64, 1 mixed.
+static sg_status run_plan(const Plan *P, Workspace *W, const DevCtx *C, const double *d_params,
+                          double guard_tol, SgOutDev *d_out) {
+    cudaStream_t s = W->stream;
+    const int prec = P->prec;
+    const int nitems = (int)P->items.size();
+    SgOutDev *outp = d_out ? d_out : (SgOutDev *)W->out.p;
+    CK(cudaMemsetAsync(W->counters.p, 0, 16 + 4 * (size_t)nitems, s));
+    if (guard_tol > 0.0) CK(cudaMemsetAsync(W->flags.p, 0, 4 * (size_t)nitems, s));
+    SgSetupArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.blocks = P->d_blocks;
+    sa.block_end = P->d_block_end;
+    sa.nblocks = (int)P->blocks.size();
+    sa.nentries = P->nentries;
+    sa.integrals = P->d_integrals;
+    sa.nintegrals = (int)P->integrals.size();
+    sa.params = d_params;
+    sa.tab32 = prec ? (float2 *)W->tab32.p : nullptr;
+    sa.tab64 = prec ? nullptr : (double2 *)W->tab64.p;
+    sa.bases = (SgBaseDev *)W->bases.p;
+    sa.flags = nullptr;
+    CK(sg_launch_setup(sa, s));
+    const double u = prec ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    SgPrepArgs pa;
+    pa.roles = P->d_roles;
+    pa.items = P->d_items;
+    pa.nitems = nitems;
+    pa.integrals = P->d_integrals;
+    pa.params = d_params;
+    pa.bases = (SgBaseDev *)W->bases.p;
+    pa.item_integral = P->d_item_integral;
+    pa.vars = (SgItemVar *)W->vars.p;
+    pa.out = outp;
+    pa.vout = (double *)W->vout.p;
+    pa.flags = (guard_tol > 0.0) ? (int *)W->flags.p : nullptr;
+    pa.unit_roundoff = u;
+    CK(sg_launch_prep(pa, s));
+    if (P->nchunks == 0) return SG_OK;
+    SgFoldArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.items = P->d_items;
+    fa.vars = (SgItemVar *)W->vars.p;
+    fa.nitems = nitems;
+    fa.pats = P->d_pats;
+    fa.pat_chunk0 = P->d_pat_chunk0;
+    fa.npat = (long long)P->pats.size();
+    fa.nchunks = P->nchunks;
+    fa.tab = prec ? W->tab32.p : W->tab64.p;
+    fa.binom = C->binom;
+    fa.slots = (SgSlot *)W->slots.p;
+    fa.work = (unsigned long long *)W->counters.p;
+    fa.item_done = (unsigned int *)((char *)W->counters.p + 16);
+    fa.bases = (SgBaseDev *)W->bases.p;
+    fa.item_integral = P->d_item_integral;
+    fa.out = outp;
+    fa.vout = (double *)W->vout.p;
+    fa.flags = (guard_tol > 0.0) ? (int *)W->flags.p : nullptr;
+    fa.skip_unflagged = nullptr;
+    fa.guard_tol = guard_tol;
+    fa.unit_roundoff = u;
+    CK(prof_mark(W, true));
+    CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C->sms), s));
+    CK(prof_mark(W, false));
+    if (prec == 1 && guard_tol > 0.0) {
+        // precision guard: recompute flagged items in FP64
+        CK(cudaMemsetAsync(W->counters.p, 0, 16 + 4 * (size_t)nitems, s));
+        sa.tab32 = nullptr;
+        sa.tab64 = (double2 *)W->tab64.p;
+        sa.flags = (int *)W->flags.p;
+        CK(sg_launch_setup(sa, s));
+        fa.tab = W->tab64.p;
+        fa.skip_unflagged = (int *)W->flags.p;
+        fa.guard_tol = 0.0;
+        fa.unit_roundoff = 1.1102230246251565e-16;
+        CK(prof_mark(W, true));
+        CK(sg_launch_fold(fa, 0, 0, fold_cfg(P, 0, C->sms), s));
+        CK(prof_mark(W, false));
+    }
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+
+static sg_status check_one(sg_rule rule, sg_family fam, int d, int q, sg_precision prec,
+                           sg_form *form) {
+    if (!rule) return SG_EINVAL;
+    if ((int)fam < 0 || (int)fam > 4) return SG_EINVAL;
+    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    if ((int)*form < 0 || (int)*form > 3) return SG_EINVAL;
+    if (*form == SG_FORM_AUTO) *form = SG_FORM_TELESCOPED;
+    if (d < 1 || q < d) return SG_EINVAL;
+    if (d > SG_MAX_D) return SG_ERANGE;
+    const int L = q - d;
+    if (L > SG_MAX_L || L + 1 > rule->max_level) return SG_ERANGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SG_ECUDA;
+    if (dev != rule->device) return SG_EINVAL;
+    return SG_OK;
+}
+
+static void fill_result(const SgOutDev &o, const Plan *P, int g, double ms, sg_result *r) {
+    r->value = o.value;
+    r->mant = o.mant;
+    r->exp2 = (int64_t)o.exp2;
+    r->cond = o.cond;
+    r->err_est = o.err_est;
+    r->points = P->points[g];
+    r->evals = P->evals[g];
+    r->seconds = ms * 1e-3;
+}
+
+extern "C" sg_status sg_count_points(sg_rule rule, int d, int q, sg_form form, uint64_t *points,
+                                     uint64_t *evals) {
+    if (!rule || !points) return SG_EINVAL;
+    if ((int)form < 0 || (int)form > 3) return SG_EINVAL;
+    if (form == SG_FORM_AUTO) form = SG_FORM_TELESCOPED;
+    if (d < 1 || q < d) return SG_EINVAL;
+    if (d > SG_MAX_D) return SG_ERANGE;
+    const int L = q - d;
+    if (L > SG_MAX_L || L + 1 > rule->max_level) return SG_ERANGE;
+    u64 pts = 0;
+    if (!count_points(rule->kind, d, L, &pts)) return SG_ERANGE;
+    if (evals) {
+        std::vector<PatSpec> specs;
+        gen_patterns(form, d, L, specs);
+        unsigned __int128 tot = 0;
+        for (auto &sp : specs) {
+            unsigned __int128 v = binom128(d, sp.r);
+            for (int t = 0; t < sp.r - 1; t++) v *= (unsigned __int128)tab_m(rule, sp.pre[t]);
+            v *= (unsigned __int128)tab_m(rule, sp.tail);
+            tot += v;
+        }
+        if (tot > (unsigned __int128)~0ull) return SG_ERANGE;
+        *evals = (u64)tot;
+    }
+    *points = pts;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_integrate_async(sg_rule rule, sg_family fam, const double *d_params, int d,
+                                        int q, sg_precision prec, sg_form form, void *stream,
+                                        sg_dev_result *d_out) {
+    if (!d_params || !d_out) return SG_EINVAL;
+    ST(check_one(rule, fam, d, q, prec, &form));
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Plan *P = nullptr;
+    std::vector<Req> reqs(1);
+    memset(reqs.data(), 0, sizeof(Req));
+    reqs[0] = Req{rule, (int)fam, d, q - d, (int)form, 0, 0};
+    ST(get_plan(reqs, prec, &P));
+    Workspace *W = nullptr;
+    ST(get_ws((cudaStream_t)stream, &W));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, 0));
+    return run_plan(P, W, C, d_params, 0.0, (SgOutDev *)d_out);
+}
+
+extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *params,
+                                  int params_on_device, int d, int q, sg_precision prec, sg_form form,
+                                  void *stream, sg_result *out) {
+    if (!params || !out) return SG_EINVAL;
+    ST(check_one(rule, fam, d, q, prec, &form));
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Plan *P = nullptr;
+    std::vector<Req> reqs(1);
+    memset(reqs.data(), 0, sizeof(Req));
+    reqs[0] = Req{rule, (int)fam, d, q - d, (int)form, 0, 0};
+    ST(get_plan(reqs, prec, &P));
+    Workspace *W = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    ST(get_ws(s, &W));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, params_on_device ? 0 : 2 * (size_t)d));
+    ST(ensure_host(W, sizeof(SgOutDev)));
+    const double *dp = params;
+    if (!params_on_device) {
+        CK(cudaMemcpyAsync(W->params.p, params, 2 * (size_t)d * sizeof(double), cudaMemcpyHostToDevice, s));
+        dp = (const double *)W->params.p;
+    }
+    CK(cudaEventRecord(W->ev0, s));
+    ST(run_plan(P, W, C, dp, 0.0, nullptr));
+    CK(cudaEventRecord(W->ev1, s));
+    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, W->ev0, W->ev1);
+    fill_result(*(SgOutDev *)W->h_pinned, P, 0, ms, out);
+    return SG_OK;
+}
+
+static sg_status batch_reqs(const sg_item *items, int n, std::vector<Req> &reqs, size_t *pool) {
+    if (!items || n < 1) return SG_EINVAL;
+    if (n > 65536) return SG_ERANGE;
+    reqs.resize(n);
+    memset(reqs.data(), 0, sizeof(Req) * n);
+    size_t need = 0;
+    for (int k = 0; k < n; k++) {
+        sg_form f = SG_FORM_AUTO;
+        ST(check_one(items[k].rule, items[k].fam, items[k].d, items[k].q, SG_PREC_FP64, &f));
+        reqs[k] = Req{items[k].rule, (int)items[k].fam, items[k].d, items[k].q - items[k].d, (int)f,
+                      (long long)items[k].param_offset, 0};
+        need = std::max(need, (size_t)items[k].param_offset + 2 * (size_t)items[k].d);
+    }
+    *pool = need;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const double *params_pool,
+                                        int params_on_device, sg_precision prec, double guard_tol,
+                                        void *stream, sg_result *out) {
+    if (!params_pool || !out) return SG_EINVAL;
+    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    if (!(guard_tol >= 0.0)) return SG_EINVAL;
+    if (prec == SG_PREC_FP64) guard_tol = 0.0;
+    std::vector<Req> reqs;
+    size_t pool = 0;
+    ST(batch_reqs(items, n, reqs, &pool));
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Plan *P = nullptr;
+    ST(get_plan(reqs, prec, &P));
+    Workspace *W = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    ST(get_ws(s, &W));
+    const bool guard = prec == SG_PREC_MIXED && guard_tol > 0.0;
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64 || guard, params_on_device ? 0 : pool));
+    ST(ensure_host(W, (size_t)P->nout * sizeof(SgOutDev)));
+    const double *dp = params_pool;
+    if (!params_on_device) {
+        CK(cudaMemcpyAsync(W->params.p, params_pool, pool * sizeof(double), cudaMemcpyHostToDevice, s));
+        dp = (const double *)W->params.p;
+    }
+    // the launch sequence is captured once per (plan, params, guard) and replayed
+    auto key = std::make_tuple((const Plan *)P, dp, guard_tol, W->epoch);
+    auto it = W->graphs.find(key);
+    if (it == W->graphs.end()) {
+        GraphEntry ge;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        sg_status st = run_plan(P, W, C, dp, guard_tol, nullptr);
+        cudaError_t ce = cudaStreamEndCapture(s, &ge.g);
+        if (st != SG_OK) return st;
+        if (ce != cudaSuccess) return SG_ECUDA;
+        if (cudaGraphInstantiate(&ge.x, ge.g, 0) != cudaSuccess) {
+            cudaGraphDestroy(ge.g);
+            return SG_ECUDA;
+        }
+        it = W->graphs.emplace(key, ge).first;
+    }
+    CK(cudaEventRecord(W->ev0, s));
+    CK(cudaGraphLaunch(it->second.x, s));
+    CK(cudaEventRecord(W->ev1, s));
+    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, (size_t)n * sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, W->ev0, W->ev1);
+    const SgOutDev *o = (const SgOutDev *)W->h_pinned;
+    for (int k = 0; k < n; k++) fill_result(o[k], P, k, ms, out + k);
+    return SG_OK;
+}
+
+extern "C" sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double *params,
+                                       int params_on_device, int d, int q, sg_precision prec,
+                                       void *stream, sg_result *out, double *dparams,
+                                       int dparams_on_device) {
+    if (!params || !out || !dparams) return SG_EINVAL;
+    sg_form form = SG_FORM_AUTO;
+    ST(check_one(rule, fam, d, q, prec, &form));
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Plan *P = nullptr;
+    std::vector<Req> reqs(1);
+    memset(reqs.data(), 0, sizeof(Req));
+    reqs[0] = Req{rule, (int)fam, d, q - d, (int)form, 0, 1};
+    ST(get_plan(reqs, prec, &P));
+    Workspace *W = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    ST(get_ws(s, &W));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, params_on_device ? 0 : 2 * (size_t)d));
+    ST(ensure_host(W, sizeof(SgOutDev) + 2 * (size_t)d * sizeof(double)));
+    const double *dp = params;
+    if (!params_on_device) {
+        CK(cudaMemcpyAsync(W->params.p, params, 2 * (size_t)d * sizeof(double), cudaMemcpyHostToDevice, s));
+        dp = (const double *)W->params.p;
+    }
+    CK(cudaEventRecord(W->ev0, s));
+    ST(run_plan(P, W, C, dp, 0.0, nullptr));
+    SgGradArgs ga;
+    ga.fam = (int)fam;
+    ga.d = d;
+    ga.L = q - d;
+    ga.params = dp;
+    ga.delta_xw = rule->d_xw;
+    ga.delta_off = P->d_delta_off;
+    ga.delta_m = P->d_delta_m;
+    ga.v = (const double *)W->vout.p;
+    ga.vstride = P->vstride;
+    ga.q = (const SgOutDev *)W->out.p;
+    ga.qh = fam == SG_FAM_OSCILLATORY ? (const SgOutDev *)W->out.p + 1 : nullptr;
+    ga.base = (const SgBaseDev *)W->bases.p;
+    ga.grad_rel = (double *)W->grad.p;
+    CK(sg_launch_grad(ga, s));
+    CK(cudaEventRecord(W->ev1, s));
+    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
+    double *hg = (double *)((char *)W->h_pinned + sizeof(SgOutDev));
+    CK(cudaMemcpyAsync(hg, W->grad.p, 2 * (size_t)d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, W->ev0, W->ev1);
+    const SgOutDev o = *(const SgOutDev *)W->h_pinned;
+    // dQ/dtheta = scale * grad_rel, scale = Q / (base + T)
+    for (int j = 0; j < 2 * d; j++) {
+        double v = hg[j];
+        if (fam != SG_FAM_OSCILLATORY) {
+            int e = 0;
+            const double m = frexp(v * o.mant / o.sum, &e);
+            v = ldexp(m, e + (int)o.exp2);
+        }
+        hg[j] = v;
+    }
+    if (dparams_on_device) {
+        CK(cudaMemcpyAsync(dparams, hg, 2 * (size_t)d * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        memcpy(dparams, hg, 2 * (size_t)d * sizeof(double));
+    }
+    fill_result(o, P, 0, ms, out);
+    out->evals = P->total_evals;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_autotune(const sg_item *items, int n, const double *params_pool,
+                                 int params_on_device, sg_precision prec, int reps, void *stream,
+                                 sg_tuning *best, double *best_ms) {
+    if (!best || reps < 1) return SG_EINVAL;
+    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    sg_tuning saved;
+    ST(sg_get_tuning(prec, &saved));
+    const int ppc[] = {2048, 8192, 32768, 131072};
+    const int cps[] = {4, 8, 16};
+    const int wpc[] = {4, 8};
+    std::vector<sg_result> res(n);
+    double best_t = 1e300;
+    sg_tuning bt = saved;
+    for (int a : ppc)
+        for (int b : cps)
+            for (int c : wpc) {
+                sg_tuning t{a, b, c};
+                ST(sg_set_tuning(prec, &t));
+                std::vector<double> ts;
+                for (int r = 0; r < reps + 1; r++) {
+                    sg_status st = sg_integrate_batch(items, n, params_pool, params_on_device, prec, 0.0,
+                                                      stream, res.data());
+                    if (st != SG_OK) {
+                        sg_set_tuning(prec, &saved);
+                        return st;
+                    }
+                    if (r) ts.push_back(res[0].seconds);
+                }
+                std::sort(ts.begin(), ts.end());
+                const double med = ts[ts.size() / 2];
+                if (med < best_t) {
+                    best_t = med;
+                    bt = t;
+                }
+            }
+    ST(sg_set_tuning(prec, &bt));
+    *best = bt;
+    if (best_ms) *best_ms = best_t * 1e3;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_profile_begin(void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace *W = nullptr;
+    ST(get_ws((cudaStream_t)stream, &W));
+    W->profiling = true;
+    W->prof_used = 0;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_profile_end(void *stream, double *fold_ms, int *launches) {
+    if (!fold_ms || !launches) return SG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace *W = nullptr;
+    ST(get_ws((cudaStream_t)stream, &W));
+    CK(cudaStreamSynchronize(W->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i < W->prof_used; i++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, W->prof[i].first, W->prof[i].second));
+        tot += ms;
+    }
+    *fold_ms = tot;
+    *launches = (int)W->prof_used;
+    W->profiling = false;
+    W->prof_used = 0;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_ceiling(sg_precision prec, int kind, void *stream, double *rate) {
+    if (!rate || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) || kind < 0 || kind > 2)
+        return SG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Workspace *W = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    ST(get_ws(s, &W));
+    ST(ensure(W, W->grad, (size_t)C->sms * 8 * 256 * sizeof(double)));
+    double work = sg_launch_ceiling(prec, kind, C->sms, (double *)W->grad.p, s);  // warm-up
+    CK(cudaGetLastError());
+    float best = 1e30f;
+    for (int r = 0; r < 3; r++) {
+        CK(cudaEventRecord(W->ev0, s));
+        work = sg_launch_ceiling(prec, kind, C->sms, (double *)W->grad.p, s);
+        CK(cudaEventRecord(W->ev1, s));
+        CK(cudaEventSynchronize(W->ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, W->ev0, W->ev1));
+        if (ms < best) best = ms;
+    }
+    *rate = work / (best * 1e-3);
+    return SG_OK;
+}

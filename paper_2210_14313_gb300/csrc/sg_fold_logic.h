@@ -1,0 +1,92 @@
+// Enumeration primitives of the fold, shared by the CUDA kernel and the
+// host-side index checker used in the tests (host and device inline code).
+#pragma once
+#include "sg_internal.h"
+
+#ifdef __CUDACC__
+#define SG_HD __host__ __device__ __forceinline__
+#else
+#define SG_HD inline
+#endif
+
+// C(n, k) from the [k][n] table (0 outside the table's domain).
+SG_HD unsigned long long sg_binom(const unsigned long long *B, int n, int k) {
+    if (n < 0 || k < 0 || k > n || n > SG_MAX_D || k >= SG_BINOM_K) return 0ull;
+#ifdef __CUDA_ARCH__
+    return __ldg(B + (size_t)k * (SG_MAX_D + 1) + n);
+#else
+    return B[(size_t)k * (SG_MAX_D + 1) + n];
+#endif
+}
+
+// Lexicographic unranking of an r-subset {i_0 < ... < i_{r-1}} of [0, d).
+// Given the previous element p, the number of subsets whose next element is
+// smaller than v is C(d-p-1, k) - C(d-v, k) with k the elements still to
+// place; v is found by binary search (C(d-v, k) decreases in v).
+SG_HD void sg_unrank_lex(unsigned long long rank, int d, int r, const unsigned long long *B,
+                         int *idx) {
+    int p = -1;
+    for (int t = 0; t < r; t++) {
+        const int k = r - t;
+        const unsigned long long total = sg_binom(B, d - p - 1, k);
+        const unsigned long long target = total - rank;
+        int lo = p + 1, hi = d - k;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sg_binom(B, d - mid, k) >= target) lo = mid;
+            else hi = mid - 1;
+        }
+        rank -= total - sg_binom(B, d - lo, k);
+        idx[t] = lo;
+        p = lo;
+    }
+}
+
+// Lexicographic successor of a subset whose last element is d-1: the
+// largest position t < r-1 that can still grow is incremented and the
+// following positions restart right after it.  Returns 0 when exhausted.
+SG_HD int sg_next_prefix(int *idx, int d, int r) {
+    int t = r - 2;
+    while (t >= 0 && idx[t] >= d - r + t) t--;
+    if (t < 0) return 0;
+    idx[t]++;
+    for (int u = t + 1; u < r; u++) idx[u] = idx[u - 1] + 1;
+    return 1;
+}
+
+// Enumerated direction -> actual direction when direction `skip` is left out.
+SG_HD int sg_actual_dir(int i, int skip) { return i + (skip >= 0 && i >= skip); }
+
+// Tail entries of a run whose last active direction takes the enumerated
+// values plast .. plast + run - 1: one or two contiguous table segments
+// (two when the actual directions jump over `skip`).
+struct SgTailSegs {
+    long long base1, base2;
+    int E1, E2;
+};
+
+SG_HD SgTailSegs sg_tail_segments(long long toff, int tm, int plast, int run, int skip) {
+    SgTailSegs s;
+    const int a0 = sg_actual_dir(plast, skip), a1 = sg_actual_dir(plast + run - 1, skip);
+    s.base1 = toff + (long long)a0 * tm;
+    if (skip > a0 && skip < a1) {
+        s.E1 = (skip - a0) * tm;
+        s.E2 = (a1 - skip) * tm;
+        s.base2 = toff + (long long)(skip + 1) * tm;
+    } else {
+        s.E1 = (a1 - a0 + 1) * tm;
+        s.E2 = 0;
+        s.base2 = 0;
+    }
+    return s;
+}
+
+// Table entry of prefix position t for prefix node tuple q (mixed radix over
+// the prefix block sizes, the last prefix position fastest).  Returns the
+// entry offset relative to the item's table and leaves q / m in *q.
+SG_HD long long sg_prefix_entry(const SgPatDev *P, int t, int dir_actual, int *q) {
+    const int m = P->pm[t];
+    const int jt = *q % m;
+    *q /= m;
+    return P->poff[t] + (long long)dir_actual * m + jt;
+}

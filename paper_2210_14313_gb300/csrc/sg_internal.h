@@ -1,0 +1,99 @@
+// Internal data layout shared by the host planner and the CUDA kernels of
+// libsg.  Not part of the public ABI (see include/sg.h).
+//
+// Vocabulary (Section 2.1 and Algorithms 3.1-3.3 of the paper):
+//  - excess k = l - 1 of a direction's level l; a direction with k = 0 sits
+//    at the centre c = 1/2 with weight 1 ("inactive");
+//  - a subgrid is a set of active directions i_1 < ... < i_r with excesses;
+//  - its first r-1 active directions form the *prefix*, the last one is the
+//    *tail* direction folded by the inner loop;
+//  - a *pattern* fixes r and the 1-D rule block of every position (which
+//    difference rule / full rule / telescoped tail rule), so all subgrids of
+//    a pattern have the same number of points and differ only in which
+//    directions are active (an r-subset of {0..d-1});
+//  - a *chunk* is a contiguous range of lexicographic ranks of those
+//    r-subsets: the unit of work stealing.
+#pragma once
+#include <stdint.h>
+
+#define SG_MAX_LEVEL 13       // 1-D rule levels 1..13 (4097 nodes, nested rules)
+#define SG_MAX_L 12           // largest excess level q - d
+#define SG_MAX_R SG_MAX_L     // active directions per subgrid
+#define SG_MAX_D 8192         // largest dimension
+#define SG_BINOM_K (SG_MAX_R + 2)
+
+// Integrand deviation kinds evaluated per point (the "G" of the kernels).
+#define SG_GK_EXPM1 0  // D = expm1(S)                 (exp-linear, gaussian(s), product peak)
+#define SG_GK_OSC 1    // D = cos(phi + S) - cos(phi)   (oscillatory)
+
+// Block kinds of a rule (node/weight lists on [0,1]).
+#define SG_BLK_DELTA 0  // J^{k+1} - J^k on the union node set, k >= 1
+#define SG_BLK_FULL 1   // J^{k+1}, k >= 1
+#define SG_BLK_TAIL 2   // J^{M+1} - J^1, M >= 1 (telescoped last direction)
+
+// One integral (or one adjoint sub-sum) as the kernels see it.
+struct SgItemDev {
+    int d;            // directions enumerated by the patterns (d or d-1)
+    int skip;         // actual direction left out of the enumeration (-1: none)
+    int gk;           // SG_GK_*
+    int out;          // index of the output record
+    long long tab;    // first table entry of the item (entries are (phi, w) pairs)
+    long long pat0;   // first pattern of the item
+    int npat;         // number of patterns
+    int pad;
+    unsigned long long chunk0;  // first chunk of the item
+    unsigned long long nchunk;  // chunks of the item
+};
+
+// Role of an item, from which the per-call values below are derived once
+// the integral's parameters and base quantities are on the device.
+#define SG_ROLE_FORWARD 0        // the integral itself
+#define SG_ROLE_FORWARD_SHIFT 1  // same sum with the phase advanced by pi/2 (oscillatory gradient)
+#define SG_ROLE_ADJOINT 2        // direction `dir` pinned at node x, other directions summed
+struct SgItemRole {
+    int role;
+    int integral;
+    int dir;
+    int pad;
+    double x;
+};
+
+// Per-call, parameter-dependent values of an item.
+struct SgItemVar {
+    double base_rel;  // the sum's centre term (1, cos(phase), ...)
+    double mult;      // item value = mult * (base_rel + T), relative to the integral's scale
+    double sin_phi, cos_phi;    // oscillatory phase of the per-point deviation
+};
+
+// One pattern of one item.
+struct SgPatDev {
+    int item;         // index into the item array
+    int r;            // active directions (prefix r-1, tail 1)
+    int A;            // prefix node tuples = prod of prefix block sizes
+    int tm;           // tail block nodes per direction
+    long long toff;   // table offset of the tail block (relative to item.tab)
+    long long poff[SG_MAX_R - 1];  // table offsets of the prefix blocks
+    int pm[SG_MAX_R - 1];          // nodes per direction of the prefix blocks
+    double coef;      // multiplier of the pattern's sum (1, or Eq. 2.6 coefficient)
+    unsigned long long nsub;   // C(d, r) subsets
+    unsigned long long spc;    // subsets per chunk
+    unsigned long long chunk0; // first global chunk of this pattern
+};
+
+// Per-chunk partial result (written once by the warp that ran the chunk).
+struct SgSlot {
+    double sum;
+    double abs;
+};
+
+// Per-output record on the device (matches sg_dev_result's first fields).
+struct SgOutDev {
+    double mant, exp2, value, cond, err_est, sum, abs_sum;
+};
+
+// Base quantities of an integral: Q = scale * (base + T), scale = exp(log_hi + log_lo).
+struct SgBaseDev {
+    double log_hi, log_lo;   // log of f(c) (exponential kinds), 0 for oscillatory
+    double base;             // 1 or cos(theta_c)
+    double sin_th, cos_th;   // theta_c for the oscillatory kind
+};

@@ -1,0 +1,614 @@
+// CUDA kernels of libsg (sm_103a).
+//
+// The hot path is sg_fold_kernel: a persistent, work-stealing kernel in
+// which each warp takes a chunk of subgrids of one pattern (Section 2.1,
+// Eq. 2.9 read as sums of tensor products of difference rules), unranks the
+// first subgrid (lexicographic r-subset of the directions), and walks the
+// chunk as *runs*: maximal sequences of subgrids that share their first r-1
+// active directions (the prefix) and differ only in the last one.  This is
+// the paper's multilevel dimension iteration (Algorithms 3.1-3.3): the
+// prefix directions are folded once per run into per-node-tuple states
+// (partial argument S_a and weight W_a, the "symbolic function" of Eq. 3.10
+// held as numbers), staged in shared memory, and every point of the run
+// then costs one table load, one add, one deviation evaluation and one FMA.
+// No point of the grid is ever stored.
+//
+// Integrands are generalised-additive, f(x) = F(theta + sum_i phi_i(x_i)),
+// with F = exp (exp-linear, gaussian, gaussian-lin, product peak via
+// phi = log psi) or F = cos (oscillatory).  Per point the kernel evaluates
+// the deviation from the centre value without cancellation:
+//   exp:  D = expm1(S)                  (relative to f(c))
+//   cos:  D = cos(phi + S) - cos(phi) = -2 sin(S/2) sin(phi + S/2)
+// and accumulates W * D.  Since every non-centre subgrid's weights sum to
+// zero, sum W f = sum W D, and the cancelling signed sum stays small.
+//
+// Reduction is deterministic: each chunk writes one (sum, abs) slot; the
+// warp that completes an item's last chunk (ticket counter) sums that item's
+// slots in chunk order with Neumaier compensation in FP64.
+#include <math.h>
+#include <stdio.h>
+
+#include "sg_fold_logic.h"
+#include "sg_kernels.h"
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void neu_add(double &s, double &c, double v) {
+    double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+// Per-direction deviation phi_i(x) - phi_i(1/2) of each family, in FP64,
+// written without cancellation.
+__device__ __forceinline__ double phi_dev(int fam, double a, double u, double x) {
+    switch (fam) {
+    case 0:  // exp-linear: a (x - 1/2)
+    case 1:  // oscillatory: a (x - 1/2)
+        return a * (x - 0.5);
+    case 2: {  // product peak: log(psi(x)/psi(1/2)), psi = 1/(a^-2 + (x-u)^2)
+        double v = x - u;
+        double eps = (0.5 - x) * (0.5 + x - 2.0 * u) / (1.0 / (a * a) + v * v);
+        return log1p(eps);
+    }
+    case 3:  // gaussian: -a^2 [(x-u)^2 - (1/2-u)^2]
+        return -a * a * (x - 0.5) * (x + 0.5 - 2.0 * u);
+    case 4:  // gaussian-lin: -a [(x-u)^2 - (1/2-u)^2]
+        return -a * (x - 0.5) * (x + 0.5 - 2.0 * u);
+    }
+    return 0.0;
+}
+
+// phi_i(1/2): the direction's share of log f(c) (exponential families) or of
+// the phase (oscillatory).
+__device__ __forceinline__ double phi_centre(int fam, double a, double u) {
+    switch (fam) {
+    case 0:
+    case 1:
+        return 0.5 * a;
+    case 2:
+        return -log(1.0 / (a * a) + (0.5 - u) * (0.5 - u));
+    case 3:
+        return -a * a * (0.5 - u) * (0.5 - u);
+    case 4:
+        return -a * (0.5 - u) * (0.5 - u);
+    }
+    return 0.0;
+}
+
+template <typename T> struct V2T;
+template <> struct V2T<float> { typedef float2 type; };
+template <> struct V2T<double> { typedef double2 type; };
+
+// Per-point deviation (the "G" evaluation).
+template <typename T, int GK> __device__ __forceinline__ T gdev(T S, T sphi, T cphi);
+template <> __device__ __forceinline__ float gdev<float, SG_GK_EXPM1>(float S, float, float) {
+    return expm1f(S);
+}
+template <> __device__ __forceinline__ double gdev<double, SG_GK_EXPM1>(double S, double, double) {
+    return expm1(S);
+}
+template <> __device__ __forceinline__ float gdev<float, SG_GK_OSC>(float S, float sphi, float cphi) {
+    float sh, ch;
+    sincosf(0.5f * S, &sh, &ch);
+    return -2.0f * sh * fmaf(sphi, ch, cphi * sh);
+}
+template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double S, double sphi, double cphi) {
+    double sh, ch;
+    sincos(0.5 * S, &sh, &ch);
+    return -2.0 * sh * fma(sphi, ch, cphi * sh);
+}
+
+// ---------------------------------------------------------------------------
+// the fold: one chunk of one pattern, processed by one warp
+// ---------------------------------------------------------------------------
+
+// Folds the points (prefix tuple a < At) x (tail entries e < E1 + E2) of one
+// run.  Tail entries come from up to two contiguous table segments (two
+// when the enumerated directions jump over a left-out direction).  Lanes are
+// spread over tail entries; when a run has fewer than 32 entries, the warp
+// splits into groups that take different prefix tuples.
+template <typename T, int GK>
+__device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict__ tab,
+                                         long long base1, int E1, long long base2, int E2,
+                                         const T *sS, const T *sW, int At, T sphi, T cphi, int lane,
+                                         double &acc, double &aabs) {
+    typedef typename V2T<T>::type V2;
+    const int E = E1 + E2;
+    const int G = E >= 32 ? 1 : 32 / E;
+    const int Eg = E >= 32 ? 32 : E;
+    const int sub = lane / Eg, el = lane - sub * Eg;
+    if (sub >= G) return;
+    for (int e0 = 0; e0 < E; e0 += Eg) {
+        const int e = e0 + el;
+        if (e >= E) break;
+        const V2 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
+        if constexpr (sizeof(T) == 4) {
+            // float folds, flushed into the double accumulators every 8 points
+            float part = 0.f, pabs = 0.f;
+            int n = 0;
+            for (int a = sub; a < At; a += G) {
+                const float S = sS[a] + te.x;
+                const float W = sW[a] * te.y;
+                const float D = gdev<float, GK>(S, sphi, cphi);
+                part = fmaf(W, D, part);
+                pabs = fmaf(fabsf(W), fabsf(D), pabs);
+                if (++n == 8) {
+                    acc += (double)part;
+                    aabs += (double)pabs;
+                    part = 0.f;
+                    pabs = 0.f;
+                    n = 0;
+                }
+            }
+            acc += (double)part;
+            aabs += (double)pabs;
+        } else {
+            for (int a = sub; a < At; a += G) {
+                const double S = sS[a] + te.x;
+                const double W = sW[a] * te.y;
+                const double D = gdev<double, GK>(S, sphi, cphi);
+                acc = fma(W, D, acc);
+                aabs = fma(fabs(W), fabs(D), aabs);
+            }
+        }
+    }
+}
+
+template <typename T, int GK>
+__device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
+                           const SgItemDev *__restrict__ I, unsigned long long c, T *sS, T *sW,
+                           int *sIdx, int lane, double &acc, double &aabs) {
+    typedef typename V2T<T>::type V2;
+    const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
+    const int d = I->d, r = P->r, skip = I->skip, Atot = P->A, tm = P->tm;
+    const SgItemVar *V = A.vars + (I - A.items);
+    const T sphi = (T)V->sin_phi, cphi = (T)V->cos_phi;
+    const unsigned long long rank = (c - P->chunk0) * P->spc;
+    unsigned long long cnt = P->nsub - rank < P->spc ? P->nsub - rank : P->spc;
+    if (lane == 0) sg_unrank_lex(rank, d, r, A.binom, sIdx);
+    __syncwarp();
+    while (cnt > 0) {
+        const int plast = sIdx[r - 1];
+        const int run = (unsigned long long)(d - plast) < cnt ? d - plast : (int)cnt;
+        const SgTailSegs seg = sg_tail_segments(P->toff, tm, plast, run, skip);
+        for (int ab = 0; ab < Atot; ab += SG_APAD) {
+            const int At = Atot - ab < SG_APAD ? Atot - ab : SG_APAD;
+            // fold the prefix directions: one state per prefix node tuple
+            for (int a = lane; a < At; a += 32) {
+                int q = ab + a;
+                T S = 0, W = 1;
+                for (int t = r - 2; t >= 0; t--) {
+                    const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
+                    S += e.x;
+                    W *= e.y;
+                }
+                sS[a] = S;
+                sW[a] = W;
+            }
+            __syncwarp();
+            fold_run<T, GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sS, sW, At, sphi, cphi, lane,
+                            acc, aabs);
+            __syncwarp();
+        }
+        cnt -= run;
+        if (cnt > 0) {
+            if (lane == 0) sg_next_prefix(sIdx, d, r);
+            __syncwarp();
+        }
+    }
+}
+
+// Value of a finished item: mult * (base_rel + T), relative to the
+// integral's scale exp(log f(c)).  Forward items write their output record
+// as Q = mant * 2^exp2; adjoint sub-sums write their relative value.
+__device__ void assemble_item(const SgItemDev *items, const SgItemVar *vars, const SgBaseDev *bases,
+                              const int *item_integral, SgOutDev *out, double *vout, int *flags,
+                              double guard_tol, double unit_roundoff, int item, double T, double AB) {
+    const SgItemDev *I = items + item;
+    const SgItemVar V = vars[item];
+    const double rel = V.mult * (V.base_rel + T);
+    const double absrel = fabs(V.mult) * (fabs(V.base_rel) + AB);
+    const int g = item_integral[item];
+    if (g < 0) {
+        vout[I->out] = rel;
+        return;
+    }
+    const SgBaseDev B = bases[g];
+    // Q = exp(log_hi + log_lo) * rel = 2^e0 * exp(r) * rel, ln 2 split in two (Cody & Waite)
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double e0 = floor(B.log_hi * 1.44269504088896338700);
+    const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
+    int e1 = 0;
+    const double mant = frexp(exp(rr) * rel, &e1);
+    SgOutDev o;
+    o.mant = mant;
+    o.exp2 = e0 + e1;
+    o.value = ldexp(mant, (int)(e0 + e1));
+    o.cond = absrel / fabs(rel);
+    o.err_est = 0.05 * unit_roundoff * o.cond;
+    o.sum = rel;
+    o.abs_sum = absrel;
+    out[I->out] = o;
+    if (flags && guard_tol > 0.0) flags[item] = o.err_est > guard_tol ? 1 : 0;
+}
+
+// Fixed-order reduction of an item's chunk slots and assembly of its value.
+__device__ void finish_item(const SgFoldArgs &A, int item, int lane) {
+    const SgItemDev *I = A.items + item;
+    double s = 0.0, c = 0.0, ab = 0.0;
+    for (unsigned long long q = lane; q < I->nchunk; q += 32) {
+        const double v = __ldcg(&A.slots[I->chunk0 + q].sum);
+        const double w = __ldcg(&A.slots[I->chunk0 + q].abs);
+        neu_add(s, c, v);
+        ab += w;
+    }
+    double S = 0.0, C = 0.0, AB = 0.0;
+    for (int t = 0; t < 32; t++) {
+        const double st = __shfl_sync(FULL_MASK, s, t);
+        const double ct = __shfl_sync(FULL_MASK, c, t);
+        const double at = __shfl_sync(FULL_MASK, ab, t);
+        neu_add(S, C, st);
+        neu_add(S, C, ct);
+        AB += at;
+    }
+    if (lane != 0) return;
+    assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, A.guard_tol,
+                  A.unit_roundoff, item, S + C, AB);
+}
+
+template <typename T>
+__global__ void sg_fold_kernel(SgFoldArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *sS = (T *)smem + (size_t)warp * 2 * SG_APAD;
+    T *sW = sS + SG_APAD;
+    int *sIdx = (int *)(smem + (size_t)nw * 2 * SG_APAD * sizeof(T)) + warp * SG_MAX_R;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(A.work, 1ull);
+        c = __shfl_sync(FULL_MASK, c, 0);
+        if (c >= A.nchunks) break;
+        // pattern of chunk c: last pattern with chunk0 <= c
+        long long lo = 0, hi = A.npat - 1;
+        while (lo < hi) {
+            long long mid = (lo + hi + 1) >> 1;
+            if (__ldg(A.pat_chunk0 + mid) <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const SgPatDev *P = A.pats + lo;
+        const int item = P->item;
+        if (A.skip_unflagged && !A.flags[item]) continue;
+        const SgItemDev *I = A.items + item;
+        double acc = 0.0, aabs = 0.0;
+        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sS, sW, sIdx, lane, acc, aabs);
+        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sS, sW, sIdx, lane, acc, aabs);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(FULL_MASK, acc, o);
+            aabs += __shfl_xor_sync(FULL_MASK, aabs, o);
+        }
+        unsigned int ticket = 0;
+        if (lane == 0) {
+            SgSlot sl;
+            sl.sum = acc * P->coef;
+            sl.abs = aabs * fabs(P->coef);
+            A.slots[c] = sl;
+            __threadfence();
+            ticket = atomicAdd(A.item_done + item, 1u);
+        }
+        ticket = __shfl_sync(FULL_MASK, ticket, 0);
+        if (ticket + 1ull == I->nchunk) {
+            __threadfence();
+            finish_item(A, item, lane);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// setup: per-integral base quantities and the (phi, w) tables
+// ---------------------------------------------------------------------------
+
+// Blocks [0, nbase) compute one integral per warp: log f(c) as a compensated
+// sum in a fixed order (lane-strided Neumaier, lanes combined in order), or
+// the oscillatory centre phase.  The remaining blocks fill table entries.
+__global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
+    const int lane = threadIdx.x & 31;
+    if ((int)blockIdx.x < nbase) {
+        const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (g >= A.nintegrals) return;
+        const SgIntegralDev G = A.integrals[g];
+        const double *a = A.params + G.param_off, *u = a + G.d;
+        double s = 0.0, c = 0.0;
+        for (int i = lane; i < G.d; i += 32) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
+        double S = 0.0, C = 0.0;
+        for (int t = 0; t < 32; t++) {
+            const double st = __shfl_sync(FULL_MASK, s, t), ct = __shfl_sync(FULL_MASK, c, t);
+            neu_add(S, C, st);
+            neu_add(S, C, ct);
+        }
+        if (lane) return;
+        SgBaseDev B;
+        if (G.fam == 1) {
+            const double two_pi = 6.28318530717958647693;
+            const double th = remainder(two_pi * u[0] + (S + C), two_pi);
+            B.log_hi = 0.0;
+            B.log_lo = 0.0;
+            sincos(th, &B.sin_th, &B.cos_th);
+            B.base = B.cos_th;
+        } else {
+            B.log_hi = S;
+            B.log_lo = C;
+            B.base = 1.0;
+            B.sin_th = 0.0;
+            B.cos_th = 1.0;
+        }
+        A.bases[g] = B;
+        return;
+    }
+    const long long stride = (long long)(gridDim.x - nbase) * blockDim.x;
+    for (long long e = (long long)(blockIdx.x - nbase) * blockDim.x + threadIdx.x; e < A.nentries;
+         e += stride) {
+        int lo = 0, hi = A.nblocks - 1;  // first block whose end > e
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(A.block_end + mid) > e) hi = mid;
+            else lo = mid + 1;
+        }
+        const SgBlockDev B = A.blocks[lo];
+        const long long local = e - (lo ? __ldg(A.block_end + lo - 1) : 0);
+        const SgIntegralDev G = A.integrals[B.integral];
+        if (A.flags && G.flag_item >= 0 && !A.flags[G.flag_item]) continue;
+        const int i = (int)(local / B.m), j = (int)(local - (long long)i * B.m);
+        const double2 xw = B.xw[j];
+        const double *p = A.params + G.param_off;
+        const double phi = phi_dev(G.fam, p[i], p[G.d + i], xw.x);
+        if (A.tab64) A.tab64[B.off + local] = make_double2(phi, xw.y);
+        if (A.tab32) A.tab32[B.off + local] = make_float2((float)phi, (float)xw.y);
+    }
+}
+
+// Per-call item values: the oscillatory phase of the per-point deviation and
+// the centre term, from the integral's centre phase theta_c (or log f(c)).
+__global__ void sg_prep_kernel(SgPrepArgs A) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= A.nitems) return;
+    const SgItemRole R = A.roles[it];
+    const SgIntegralDev G = A.integrals[R.integral];
+    const SgBaseDev B = A.bases[R.integral];
+    SgItemVar V;
+    double sn = B.sin_th, cs = B.cos_th;
+    if (R.role != SG_ROLE_FORWARD && G.fam == 1) {  // advance the phase by pi/2
+        const double t = sn;
+        sn = cs;
+        cs = -t;
+    }
+    double shift = 0.0;
+    if (R.role == SG_ROLE_ADJOINT) {
+        const double *p = A.params + G.param_off;
+        shift = phi_dev(G.fam, p[R.dir], p[G.d + R.dir], R.x);
+    }
+    if (G.fam == 1) {
+        // phase theta + shift: rotate (sin, cos) by the shift
+        double ss, cc;
+        sincos(shift, &ss, &cc);
+        V.sin_phi = sn * cc + cs * ss;
+        V.cos_phi = cs * cc - sn * ss;
+        V.base_rel = V.cos_phi;
+        V.mult = 1.0;
+    } else {
+        V.sin_phi = 0.0;
+        V.cos_phi = 1.0;
+        V.base_rel = 1.0;
+        V.mult = exp(shift);
+    }
+    A.vars[it] = V;
+    if (A.items[it].nchunk == 0)
+        assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, 0.0,
+                      A.unit_roundoff, it, 0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint assembly: one thread per parameter
+// ---------------------------------------------------------------------------
+
+// dQ/dtheta = sum_p W_p h(x_p), h = g(x_i) F_h(x_p) with F_h = f (exponential
+// families) or cos(phase + pi/2) (oscillatory, d/da_i).  Splitting
+// g(x_i) = g(c) + (g(x_i) - g(c)):
+//   dQ/dtheta / scale = g(c) Q_h/scale
+//        + sum_{k, j} dw_{k,j} (g(x_j) - g(c)) V_{i,k,j},
+// where V_{i,k,j} is the Smolyak sum over the other directions (budget
+// L - k) with direction i at node j of the level-(k+1) difference rule,
+// computed by the fold kernel as adjoint sub-sums.
+__device__ __forceinline__ void grad_factor(int fam, bool is_u, double a, double u, double x,
+                                            double *g) {
+    switch (fam) {
+    case 0:
+        *g = is_u ? 0.0 : x;
+        return;
+    case 1:
+        *g = is_u ? 0.0 : x;
+        return;
+    case 2: {
+        const double den = 1.0 / (a * a) + (x - u) * (x - u);
+        *g = is_u ? 2.0 * (x - u) / den : 2.0 / (a * a * a) / den;
+        return;
+    }
+    case 3:
+        *g = is_u ? 2.0 * a * a * (x - u) : -2.0 * a * (x - u) * (x - u);
+        return;
+    case 4:
+        *g = is_u ? 2.0 * a * (x - u) : -(x - u) * (x - u);
+        return;
+    }
+    *g = 0.0;
+}
+
+__global__ void sg_grad_kernel(SgGradArgs A) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 2 * A.d) return;
+    const bool is_u = j >= A.d;
+    const int i = is_u ? j - A.d : j;
+    const double a = A.params[i], u = A.params[A.d + i];
+    if (A.fam == 1 && is_u) {  // oscillatory: only u_0 matters, d/du_0 = 2 pi Q_h
+        A.grad_rel[j] = (i == 0) ? 6.28318530717958647693 * A.qh->sum : 0.0;
+        return;
+    }
+    if (A.fam == 0 && is_u) {
+        A.grad_rel[j] = 0.0;
+        return;
+    }
+    const double qrel = (A.fam == 1) ? A.qh->sum : A.q->sum;
+    double gc;
+    grad_factor(A.fam, is_u, a, u, 0.5, &gc);
+    double s = 0.0, c = 0.0;
+    neu_add(s, c, gc * qrel);
+    const double *v = A.v + (size_t)i * A.vstride;
+    int col = 0;
+    for (int k = 1; k <= A.L; k++) {
+        const double2 *xw = A.delta_xw + A.delta_off[k];
+        for (int jn = 0; jn < A.delta_m[k]; jn++, col++) {
+            double gx;
+            grad_factor(A.fam, is_u, a, u, xw[jn].x, &gx);
+            neu_add(s, c, xw[jn].y * (gx - gc) * v[col]);
+        }
+    }
+    A.grad_rel[j] = s + c;
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+
+cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s) {
+    const int threads = 256;
+    const int nbase = (a.nintegrals + 7) / 8;
+    long long eblocks = (a.nentries + threads - 1) / threads;
+    if (eblocks > 152 * 16) eblocks = 152 * 16;
+    if (eblocks < 1) eblocks = 1;
+    sg_setup_kernel<<<(unsigned)(nbase + eblocks), threads, 0, s>>>(a, nbase);
+    return cudaGetLastError();
+}
+
+static size_t fold_smem(int prec, int warps) {
+    const size_t tsz = prec ? sizeof(float) : sizeof(double);
+    return (size_t)warps * (2 * SG_APAD * tsz + SG_MAX_R * sizeof(int));
+}
+
+int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
+    (void)gk;
+    int n = 0;
+    const size_t sm = fold_smem(prec, warps_per_cta);
+    if (prec)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel<float>, 32 * warps_per_cta, sm);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel<double>, 32 * warps_per_cta, sm);
+    return n;
+}
+
+cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cfg, cudaStream_t s) {
+    (void)gk;
+    const size_t sm = fold_smem(prec, cfg.warps_per_cta);
+    if (prec) sg_fold_kernel<float><<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
+    else sg_fold_kernel<double><<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t sg_launch_prep(const SgPrepArgs &a, cudaStream_t s) {
+    const int threads = 128;
+    sg_prep_kernel<<<(a.nitems + threads - 1) / threads, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t sg_launch_grad(const SgGradArgs &a, cudaStream_t s) {
+    const int threads = 128;
+    const int blocks = (2 * a.d + threads - 1) / threads;
+    sg_grad_kernel<<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ceiling microbenchmarks
+// ---------------------------------------------------------------------------
+
+// The fold's inner loop on register-resident data: 8 tail entries per
+// thread, an argument drifting per sweep so nothing can be hoisted.
+template <typename T, int GK>
+__global__ void __launch_bounds__(256) sg_ceiling_kernel(int sweeps, double *out) {
+    T dl[8], wl[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        dl[k] = (T)((k - 3.5) * 0.05 + threadIdx.x * 1e-5);
+        wl[k] = (T)((k & 1) ? -0.25 : 0.3);
+    }
+    T S = (T)(blockIdx.x * 1e-6), W = (T)0.7;
+    const T sphi = (T)0.3, cphi = (T)0.95;
+    double acc = 0.0, aabs = 0.0;
+    for (int it = 0; it < sweeps; it++) {
+        if constexpr (sizeof(T) == 4) {
+            float part = 0.f, pabs = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const float s = S + dl[k], w = W * wl[k];
+                const float D = gdev<float, GK>(s, sphi, cphi);
+                part = fmaf(w, D, part);
+                pabs = fmaf(fabsf(w), fabsf(D), pabs);
+            }
+            acc += (double)part;
+            aabs += (double)pabs;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const double s = S + dl[k], w = W * wl[k];
+                const double D = gdev<double, GK>(s, sphi, cphi);
+                acc = fma(w, D, acc);
+                aabs = fma(fabs(w), fabs(D), aabs);
+            }
+        }
+        S += (T)1e-7;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc + 1e-30 * aabs;
+}
+
+// Eight independent fused multiply-add chains per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) sg_fma_kernel(int sweeps, double *out) {
+    T x[8];
+    const T a = (T)0.999999, b = (T)1e-7;
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x + k);
+    for (int it = 0; it < sweeps; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = x[k] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
+}
+
+double sg_launch_ceiling(int prec, int kind, int sms, double *d_out, cudaStream_t s) {
+    const int threads = 256, blocks = sms * 8;
+    int sweeps;
+    double per = 8.0 * threads * (double)blocks;
+    if (kind == 2) {
+        sweeps = prec ? 1 << 16 : 1 << 11;
+        if (prec) sg_fma_kernel<float><<<blocks, threads, 0, s>>>(sweeps, d_out);
+        else sg_fma_kernel<double><<<blocks, threads, 0, s>>>(sweeps, d_out);
+        per *= 2.0;  // two flops per fused multiply-add
+    } else {
+        sweeps = prec ? 1 << 11 : 1 << 7;
+        if (prec) {
+            if (kind == 1) sg_ceiling_kernel<float, SG_GK_OSC><<<blocks, threads, 0, s>>>(sweeps, d_out);
+            else sg_ceiling_kernel<float, SG_GK_EXPM1><<<blocks, threads, 0, s>>>(sweeps, d_out);
+        } else {
+            if (kind == 1) sg_ceiling_kernel<double, SG_GK_OSC><<<blocks, threads, 0, s>>>(sweeps, d_out);
+            else sg_ceiling_kernel<double, SG_GK_EXPM1><<<blocks, threads, 0, s>>>(sweeps, d_out);
+        }
+    }
+    return per * sweeps;
+}

@@ -1,0 +1,114 @@
+// Launch wrappers of libsg's CUDA kernels (host-callable, no torch types).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sg_internal.h"
+
+// One 1-D rule block attached to an integral's table: m nodes per direction
+// for d directions, entries (phi_i(x_j), w_j) at table[off + i*m + j].
+struct SgBlockDev {
+    long long off;        // absolute table entry offset
+    int m;                // nodes per direction
+    int integral;         // integral index (params, family)
+    const double2 *xw;    // the rule block's (x_j, w_j) on the device
+};
+
+// Per integral data the setup kernel needs.
+struct SgIntegralDev {
+    int fam;              // sg_family
+    int d;
+    long long param_off;  // offset of the 2d parameters in the pool
+    int flag_item;        // item whose guard flag gates the FP64 table build (-1: always)
+    int pad;
+};
+
+struct SgSetupArgs {
+    const SgBlockDev *blocks;
+    const long long *block_end;  // inclusive prefix sum of block entry counts
+    int nblocks;
+    long long nentries;
+    const SgIntegralDev *integrals;
+    int nintegrals;
+    const double *params;
+    float2 *tab32;                // may be NULL
+    double2 *tab64;               // may be NULL
+    SgBaseDev *bases;             // one per integral
+    const int *flags;             // guard flags per item (NULL: build all)
+};
+
+struct SgFoldArgs {
+    const SgItemDev *items;
+    const SgItemVar *vars;           // per item, filled by the prep kernel
+    int nitems;
+    const SgPatDev *pats;
+    const unsigned long long *pat_chunk0;  // per pattern, ascending
+    long long npat;
+    unsigned long long nchunks;
+    const void *tab;                 // float2* or double2*
+    const unsigned long long *binom; // [k][n] table
+    SgSlot *slots;                   // per chunk
+    unsigned long long *work;        // work-stealing counter (zeroed before launch)
+    unsigned int *item_done;         // per item chunk tickets (zeroed before launch)
+    const SgBaseDev *bases;          // per integral, for the final assembly
+    const int *item_integral;        // per item: integral index (-1: adjoint sub-sum)
+    SgOutDev *out;                   // per output
+    double *vout;                    // adjoint sub-sum values (per output index)
+    int *flags;                      // guard flags per item (written when guard_tol > 0)
+    const int *skip_unflagged;       // if non-NULL: only items with flags[item] != 0 are run
+    double guard_tol;
+    double unit_roundoff;            // 2^-24 or 2^-53
+};
+
+#define SG_APAD 128  // prefix states per warp held in shared memory
+
+// Grid sizing of the persistent fold kernel.
+struct SgLaunchCfg {
+    int ctas;
+    int warps_per_cta;
+};
+
+// Binomial table C(n, k), n <= SG_MAX_D, k < SG_BINOM_K (saturating), layout [k][n].
+void sg_fill_binomials(unsigned long long *host_table);
+
+cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s);
+
+struct SgPrepArgs {
+    const SgItemRole *roles;
+    const SgItemDev *items;
+    int nitems;
+    const SgIntegralDev *integrals;
+    const double *params;
+    const SgBaseDev *bases;
+    const int *item_integral;
+    SgItemVar *vars;
+    // items without any chunk (nothing beyond the centre term) are finished here
+    SgOutDev *out;
+    double *vout;
+    int *flags;
+    double unit_roundoff;
+};
+// Fills the per-call item values (phases, multipliers) after the setup kernel.
+cudaError_t sg_launch_prep(const SgPrepArgs &a, cudaStream_t s);
+// prec: 0 = double tables, 1 = float tables.
+cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cfg, cudaStream_t s);
+// Resident CTAs per SM of the fold kernel for this precision / warps per CTA.
+int sg_fold_occupancy(int prec, int gk, int warps_per_cta);
+
+struct SgGradArgs {
+    int fam, d, L;
+    const double *params;        // 2d parameters (device)
+    const double2 *delta_xw;     // DELTA blocks of the rule, concatenated for k = 1..L
+    const int *delta_off;        // offsets of block k in delta_xw (k = 1..L), and m_k
+    const int *delta_m;
+    const double *v;             // adjoint sub-sums, [i][sum_k m_k]
+    int vstride;
+    const SgOutDev *q;           // forward value record (relative, see below)
+    const SgOutDev *qh;          // phase-shifted forward value (oscillatory) or NULL
+    const SgBaseDev *base;
+    double *grad_rel;            // out: 2d values, dQ/dtheta / scale
+};
+cudaError_t sg_launch_grad(const SgGradArgs &a, cudaStream_t s);
+
+// Ceiling microbenchmarks (see sg_ceiling in include/sg.h).  Returns the
+// number of points (or flops) one launch performs.
+double sg_launch_ceiling(int prec, int kind, int sms, double *d_out, cudaStream_t s);

@@ -1,0 +1,335 @@
+// Host planner of libsg (see sg_plan.h).
+#include "sg_plan.h"
+#include "sg_rules.h"
+
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+
+unsigned __int128 binom128(long long n, int k) {
+    if (k < 0 || n < k) return 0;
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; i++) {
+        r = r * (unsigned __int128)(n - k + i) / (unsigned __int128)i;
+        if (r > ((unsigned __int128)1 << 120)) return (unsigned __int128)1 << 127;
+    }
+    return r;
+}
+
+
+
+void compositions(int K, int r, std::vector<int> &cur, std::vector<std::vector<int>> &out) {
+    if (r == 0) {
+        if (K == 0) out.push_back(cur);
+        return;
+    }
+    for (int a = 1; a <= K - (r - 1); a++) {
+        cur.push_back(a);
+        compositions(K - a, r - 1, cur, out);
+        cur.pop_back();
+    }
+}
+
+// Pattern list of one Smolyak sum over d directions with excess budget L.
+//  difference:  every composition (k_1..k_r) of K <= L; all blocks DELTA
+//  telescoped:  prefix compositions of K_P <= L-1 with DELTA blocks; the
+//               last direction folds TAIL(L - K_P) = J^{L-K_P+1} - J^1
+//  combination: compositions of K in [max(1, L-d+1), L] with FULL blocks and
+//               coefficient (-1)^(L-K) C(d-1, L-K) (Eq. 2.6; the all-centre
+//               subgrid contributes no deviation)
+void gen_patterns(int form, int d, int L, std::vector<PatSpec> &out) {
+    out.clear();
+    std::vector<int> cur;
+    auto add = [&](const std::vector<int> &pre, int pre_bk, BlockRef tail, double coef) {
+        PatSpec p;
+        p.r = (int)pre.size() + 1;
+        for (size_t t = 0; t < pre.size(); t++) p.pre[t] = BlockRef{pre_bk, pre[t]};
+        p.tail = tail;
+        p.coef = coef;
+        out.push_back(p);
+    };
+    if (form == SG_FORM_TELESCOPED) {
+        for (int KP = 0; KP <= L - 1; KP++) {
+            BlockRef tail{SG_BLK_TAIL, L - KP};
+            if (KP == 0) {
+                add(std::vector<int>(), SG_BLK_DELTA, tail, 1.0);
+                continue;
+            }
+            for (int rp = 1; rp <= std::min(KP, d - 1); rp++) {
+                std::vector<std::vector<int>> comps;
+                compositions(KP, rp, cur, comps);
+                for (auto &c : comps) add(c, SG_BLK_DELTA, tail, 1.0);
+            }
+        }
+        return;
+    }
+    int Klo = 1;
+    if (form == SG_FORM_COMBINATION) Klo = std::max(1, L - d + 1);
+    for (int K = Klo; K <= L; K++) {
+        double coef = 1.0;
+        if (form == SG_FORM_COMBINATION) {
+            coef = (double)binom128(d - 1, L - K);
+            if ((L - K) % 2) coef = -coef;
+        }
+        int bk = form == SG_FORM_COMBINATION ? SG_BLK_FULL : SG_BLK_DELTA;
+        for (int r = 1; r <= std::min(K, d); r++) {
+            std::vector<std::vector<int>> comps;
+            compositions(K, r, cur, comps);
+            for (auto &c : comps) {
+                std::vector<int> pre(c.begin(), c.end() - 1);
+                add(pre, bk, BlockRef{bk, c.back()}, coef);
+            }
+        }
+    }
+}
+
+
+
+int tab_m(sg_rule rule, BlockRef b) { return (int)rule->x[b.bk][b.k].size(); }
+
+// n_d^q of Eq. 2.6: sum over the combination-form multi-indices of
+// prod n_{l_i}, as a polynomial in the excess, direction by direction.
+bool count_points(int kind, int d, int L, u64 *out) {
+    std::vector<unsigned __int128> c(L + 1, 0), nc(L + 1);
+    c[0] = 1;
+    for (int i = 0; i < d; i++) {
+        std::fill(nc.begin(), nc.end(), 0);
+        for (int K = 0; K <= L; K++)
+            for (int k = 0; K + k <= L; k++) nc[K + k] += c[K] * (unsigned __int128)sg_level_nodes(kind, k + 1);
+        for (int K = 0; K <= L; K++) {
+            c[K] = nc[K];
+            if (c[K] > ((unsigned __int128)1 << 100)) return false;
+        }
+    }
+    unsigned __int128 t = 0;
+    for (int K = std::max(0, L - d + 1); K <= L; K++) t += c[K];
+    if (t > (unsigned __int128)~0ull) return false;
+    *out = (u64)t;
+    return true;
+}
+
+struct ItemBuild {
+    SgItemDev it;
+    SgItemRole role;
+    int integral;   // -1 for adjoint sub-sums
+    int L, form;
+    std::vector<PatSpec> specs;
+    u64 evals = 0;
+};
+
+
+void plan_free_host(Plan *P) { delete P; }
+
+// Builds the items, table layout, patterns and chunks of a list of integrals.
+sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tuning &tune, int sms,
+                          Plan **out) {
+    Plan *P = new Plan();
+    P->reqs = reqs;
+    P->prec = prec;
+    P->tune = tune;
+    const int nint = (int)reqs.size();
+    std::vector<ItemBuild> ib;
+    std::vector<std::map<BlockRef, long long>> relmap(nint);  // block -> offset in the integral's table
+    long long tab_cursor = 0, vcursor = 0;
+    int shift_out = nint;
+    for (int g = 0; g < nint; g++) {
+        const Req &R = reqs[g];
+        sg_rule rule = R.rule;
+        u64 pts = 0;
+        if (!count_points(rule->kind, R.d, R.L, &pts)) {
+            plan_free_host(P);
+            return SG_ERANGE;
+        }
+        P->points.push_back(pts);
+        P->max_d = std::max(P->max_d, R.d);
+        const int gk = R.fam == SG_FAM_OSCILLATORY ? SG_GK_OSC : SG_GK_EXPM1;
+        const size_t first = ib.size();
+        auto new_item = [&](int role, int dir, double x, int d_item, int skip, int L_item, int o) {
+            ItemBuild b;
+            memset(&b.it, 0, sizeof(b.it));
+            b.it.d = d_item;
+            b.it.skip = skip;
+            b.it.gk = gk;
+            b.it.out = o;
+            b.it.tab = tab_cursor;
+            b.role.role = role;
+            b.role.integral = g;
+            b.role.dir = dir;
+            b.role.pad = 0;
+            b.role.x = x;
+            b.integral = role == SG_ROLE_ADJOINT ? -1 : g;
+            b.L = L_item;
+            b.form = R.form;
+            gen_patterns(R.form, d_item, L_item, b.specs);
+            ib.push_back(b);
+        };
+        new_item(SG_ROLE_FORWARD, -1, 0.0, R.d, -1, R.L, g);
+        if (R.grad) {
+            if (R.fam == SG_FAM_OSCILLATORY)
+                new_item(SG_ROLE_FORWARD_SHIFT, -1, 0.0, R.d, -1, R.L, shift_out++);
+            int vstride = 0;
+            P->delta_off.assign(R.L + 1, 0);
+            P->delta_m.assign(R.L + 1, 0);
+            for (int k = 1; k <= R.L; k++) {
+                P->delta_off[k] = rule->off[SG_BLK_DELTA][k];
+                P->delta_m[k] = (int)rule->x[SG_BLK_DELTA][k].size();
+                vstride += P->delta_m[k];
+            }
+            P->vstride = vstride;
+            for (int i = 0; i < R.d; i++) {
+                int col = 0;
+                for (int k = 1; k <= R.L; k++)
+                    for (int j = 0; j < P->delta_m[k]; j++, col++)
+                        new_item(SG_ROLE_ADJOINT, i, rule->x[SG_BLK_DELTA][k][j], R.d - 1, i, R.L - k,
+                                 (int)(vcursor + (long long)i * vstride + col));
+            }
+            vcursor += (long long)R.d * vstride;
+        }
+        // table blocks: every block an item of this integral refers to
+        std::vector<BlockRef> refs;
+        for (size_t t = first; t < ib.size(); t++)
+            for (auto &sp : ib[t].specs) {
+                for (int q = 0; q < sp.r - 1; q++) refs.push_back(sp.pre[q]);
+                refs.push_back(sp.tail);
+            }
+        std::sort(refs.begin(), refs.end());
+        refs.erase(std::unique(refs.begin(), refs.end()), refs.end());
+        long long cur = 0;
+        for (auto &b : refs) {
+            if (b.k < 1 || b.k >= rule->max_level) {
+                plan_free_host(P);
+                return SG_ERANGE;
+            }
+            const int m = tab_m(rule, b);
+            relmap[g][b] = cur;
+            SgBlockDev bd;
+            bd.off = tab_cursor + cur;
+            bd.m = m;
+            bd.integral = g;
+            bd.xw = rule->d_xw + rule->off[b.bk][b.k];
+            P->blocks.push_back(bd);
+            P->block_refs.push_back(b);
+            cur += (long long)R.d * m;
+            P->block_end.push_back(tab_cursor + cur);
+        }
+        SgIntegralDev G;
+        G.fam = R.fam;
+        G.d = R.d;
+        G.param_off = R.param_off;
+        G.flag_item = -1;
+        G.pad = 0;
+        P->integrals.push_back(G);
+        for (size_t t = first; t < ib.size(); t++) {
+            ItemBuild &b = ib[t];
+            for (auto &sp : b.specs) {
+                const unsigned __int128 ns = binom128(b.it.d, sp.r);
+                if (ns > ((unsigned __int128)1 << 62)) {
+                    plan_free_host(P);
+                    return SG_ERANGE;
+                }
+                unsigned __int128 A = 1;
+                for (int q = 0; q < sp.r - 1; q++) A *= (unsigned __int128)tab_m(rule, sp.pre[q]);
+                const unsigned __int128 ev = ns * A * (unsigned __int128)tab_m(rule, sp.tail);
+                if (A > (1u << 30) || ev > ((unsigned __int128)1 << 62)) {
+                    plan_free_host(P);
+                    return SG_ERANGE;
+                }
+                b.evals += (u64)ev;
+            }
+        }
+        P->evals.push_back(ib[first].evals);
+        tab_cursor += cur;
+    }
+    P->nentries = tab_cursor;
+    P->nv = vcursor;
+    P->nout = shift_out;
+    // largest items first (longest-processing-time order of the work queue)
+    std::vector<int> order(ib.size());
+    for (size_t t = 0; t < ib.size(); t++) order[t] = (int)t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return ib[x].evals > ib[y].evals; });
+    u64 total = 0;
+    for (auto &b : ib) total += b.evals;
+    P->total_evals = total;
+    // chunk size: enough chunks to keep every resident warp busy, few enough slots
+    const u64 warps = (u64)sms * tune.ctas_per_sm * tune.warps_per_cta;
+    u64 target = (u64)tune.points_per_chunk;
+    const u64 balance = total / (4 * std::max<u64>(warps, 1)) + 1;
+    if (balance < target) target = std::max<u64>(balance, 64);
+    const u64 max_chunks = 1ull << 24;
+    if (total / target > max_chunks) target = total / max_chunks + 1;
+    u64 chunk = 0;
+    for (size_t q = 0; q < order.size(); q++) {
+        ItemBuild &b = ib[order[q]];
+        const int g = b.role.integral;
+        sg_rule rule = reqs[g].rule;
+        b.it.pat0 = (long long)P->pats.size();
+        b.it.chunk0 = chunk;
+        for (auto &sp : b.specs) {
+            SgPatDev pd;
+            memset(&pd, 0, sizeof(pd));
+            pd.item = (int)q;
+            pd.r = sp.r;
+            pd.nsub = (u64)binom128(b.it.d, sp.r);
+            if (pd.nsub == 0) continue;
+            u64 A = 1;
+            for (int t = 0; t < sp.r - 1; t++) {
+                pd.pm[t] = tab_m(rule, sp.pre[t]);
+                pd.poff[t] = relmap[g].at(sp.pre[t]);
+                A *= (u64)pd.pm[t];
+            }
+            pd.A = (int)A;
+            pd.tm = tab_m(rule, sp.tail);
+            pd.toff = relmap[g].at(sp.tail);
+            pd.coef = sp.coef;
+            pd.spc = std::max<u64>(1, target / (A * (u64)pd.tm));
+            pd.chunk0 = chunk;
+            chunk += (pd.nsub + pd.spc - 1) / pd.spc;
+            P->pats.push_back(pd);
+            P->pat_chunk0.push_back(pd.chunk0);
+        }
+        b.it.npat = (int)((long long)P->pats.size() - b.it.pat0);
+        b.it.nchunk = chunk - b.it.chunk0;
+        P->items.push_back(b.it);
+        P->roles.push_back(b.role);
+        P->item_integral.push_back(b.integral);
+        if (b.role.role == SG_ROLE_FORWARD) P->integrals[g].flag_item = (int)q;
+    }
+    P->nchunks = chunk;
+    if (P->pats.empty()) {  // keep the device arrays non-empty
+        SgPatDev pd;
+        memset(&pd, 0, sizeof(pd));
+        P->pats.push_back(pd);
+        P->pat_chunk0.push_back(~0ull);
+    }
+    if (P->blocks.empty()) {
+        SgBlockDev bd;
+        memset(&bd, 0, sizeof(bd));
+        bd.m = 1;
+        P->blocks.push_back(bd);
+        P->block_refs.push_back(BlockRef{0, 0});
+        P->block_end.push_back(0);
+    }
+    *out = P;
+    return SG_OK;
+}
+
+
+void sg_fill_binomials(unsigned long long *B) {
+    const unsigned long long SAT = ~0ull;
+    for (int k = 0; k < SG_BINOM_K; k++)
+        for (int n = 0; n <= SG_MAX_D; n++) {
+            unsigned long long v;
+            if (k == 0) v = 1;
+            else if (n < k) v = 0;
+            else {
+                // C(n,k) = C(n-1,k-1) + C(n-1,k), saturating
+                const unsigned long long x = B[(size_t)(k - 1) * (SG_MAX_D + 1) + n - 1];
+                const unsigned long long y = B[(size_t)k * (SG_MAX_D + 1) + n - 1];
+                v = (x == SAT || y == SAT || x > SAT - y) ? SAT : x + y;
+            }
+            B[(size_t)k * (SG_MAX_D + 1) + n] = v;
+        }
+}
+

@@ -1,0 +1,50 @@
+"""ctypes access to the host-side index checker of the fold kernel (tests only)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+CSRC = os.path.join(ROOT, "paper_2210_14313_gb300", "csrc")
+LIB = os.path.join(HERE, "libsgcheck.so")
+SRCS = [os.path.join(HERE, "sg_index_check.cpp"), os.path.join(CSRC, "sg_plan.cpp"),
+        os.path.join(CSRC, "sg_rules.cpp")]
+_lib = None
+
+
+def build():
+    deps = SRCS + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    if not os.path.exists(LIB) or any(os.path.getmtime(p) > os.path.getmtime(LIB) for p in deps):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-I/usr/local/cuda/include", "-o", tmp, *SRCS])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(LIB)
+        _lib.chk_run.restype = ctypes.c_int
+    return _lib
+
+
+def run(kind, fam, params, d, L, form=2, grad=0, ppc=2048, ctas_per_sm=8, warps=8):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros(8)
+    nv = ctypes.c_longlong(0)
+    cap = 2 * d * 64 if grad else 1
+    v = np.zeros(max(cap, 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = _load().chk_run(kind, fam, p.ctypes.data_as(dp), d, L, form, grad, ppc, ctas_per_sm, warps,
+                         out.ctypes.data_as(dp), v.ctypes.data_as(dp) if grad else None,
+                         ctypes.byref(nv))
+    if rc != 0:
+        raise RuntimeError("chk_run failed with %d" % rc)
+    return dict(rel=out[0], logscale=out[1], violations=int(out[2]), badpairs=int(out[3]),
+                evals=int(out[4]), chunks=int(out[5]), plan_evals=int(out[6]), rel_shift=out[7],
+                v=v[:nv.value])

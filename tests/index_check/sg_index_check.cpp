@@ -1,0 +1,257 @@
+// Host-side check of the fold kernel's index arithmetic (test infrastructure).
+//
+// Builds a plan with the library's own planner, then walks every chunk
+// sequentially with the same enumeration primitives the CUDA kernel uses
+// (sg_fold_logic.h): unranking, runs, tail segments, prefix entries.  Every
+// table access is checked against the bounds of the block it must fall in,
+// and the warp's lane split of a run (prefix groups x tail entries) is
+// replayed to check that each (prefix tuple, tail entry) pair is visited
+// exactly once.  The sums are formed in double so that the tests can also
+// compare them with the oracle; this is a check of the enumeration, not a
+// second implementation of the method (no CUDA code path calls it).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../paper_2210_14313_gb300/csrc/sg_fold_logic.h"
+#include "../../paper_2210_14313_gb300/csrc/sg_plan.h"
+#include "../../paper_2210_14313_gb300/csrc/sg_rules.h"
+
+namespace {
+
+double phi_dev(int fam, double a, double u, double x) {
+    switch (fam) {
+    case 0:
+    case 1: return a * (x - 0.5);
+    case 2: {
+        double v = x - u;
+        return log1p((0.5 - x) * (0.5 + x - 2.0 * u) / (1.0 / (a * a) + v * v));
+    }
+    case 3: return -a * a * (x - 0.5) * (x + 0.5 - 2.0 * u);
+    case 4: return -a * (x - 0.5) * (x + 0.5 - 2.0 * u);
+    }
+    return 0;
+}
+
+double phi_c(int fam, double a, double u) {
+    switch (fam) {
+    case 0:
+    case 1: return 0.5 * a;
+    case 2: return -log(1.0 / (a * a) + (0.5 - u) * (0.5 - u));
+    case 3: return -a * a * (0.5 - u) * (0.5 - u);
+    case 4: return -a * (0.5 - u) * (0.5 - u);
+    }
+    return 0;
+}
+
+void neu(double &s, double &c, double v) {
+    double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Returns 0 on success; out[0] = forward value relative to exp(log f(c))
+// (i.e. base + T times the multiplier), out[1] = log f(c) (exponential
+// families), out[2] = number of bound violations, out[3] = pairs visited
+// other than exactly once, out[4] = evaluations, out[5] = chunks,
+// out[6] = evaluations the plan claims.  vout receives the adjoint sub-sums
+// (nv entries, may be NULL); nv_out their count.
+int chk_run(int kind, int fam, const double *params, int d, int L, int form, int grad, int ppc,
+            int ctas_per_sm, int warps, double *out, double *vout, long long *nv_out) {
+    sg_rule_s rule;
+    rule.kind = kind;
+    rule.max_level = L + 2 > SG_MAX_LEVEL ? SG_MAX_LEVEL : L + 2;
+    std::vector<double> tx(2 * 4097 + 2), tw(2 * 4097 + 2);
+    int off = 0;
+    for (int bk = 0; bk < 3; bk++)
+        for (int k = 1; k < rule.max_level; k++) {
+            int n = sg_block(kind, bk, k, tx.data(), tw.data());
+            rule.x[bk][k].assign(tx.begin(), tx.begin() + n);
+            rule.w[bk][k].assign(tw.begin(), tw.begin() + n);
+            rule.off[bk][k] = off;
+            off += n;
+        }
+    std::vector<Req> reqs(1);
+    reqs[0] = Req{&rule, fam, d, L, form, 0, grad};
+    sg_tuning t{ppc, ctas_per_sm, warps};
+    Plan *P = nullptr;
+    if (build_plan_host(reqs, 0, t, 152, &P) != SG_OK) return 1;
+
+    // table, filled from the host block lists
+    std::vector<double2> tab(P->nentries > 0 ? P->nentries : 1);
+    std::vector<int> owner(tab.size(), -1);  // block index of every entry
+    for (size_t b = 0; b < P->blocks.size() && P->nentries > 0; b++) {
+        const SgBlockDev &B = P->blocks[b];
+        const BlockRef R = P->block_refs[b];
+        const long long begin = b ? P->block_end[b - 1] : 0;
+        if (B.off != begin) return 2;
+        const std::vector<double> &x = rule.x[R.bk][R.k], &w = rule.w[R.bk][R.k];
+        for (int i = 0; i < d; i++)
+            for (int j = 0; j < B.m; j++) {
+                const long long e = B.off + (long long)i * B.m + j;
+                if (e >= P->block_end[b]) return 3;
+                tab[e].x = phi_dev(fam, params[i], params[d + i], x[j]);
+                tab[e].y = w[j];
+                owner[e] = (int)b;
+            }
+    }
+    // centre quantities
+    double ls = 0, lc = 0;
+    for (int i = 0; i < d; i++) neu(ls, lc, phi_c(fam, params[i], params[d + i]));
+    double sth = 0, cth = 1;
+    if (fam == 1) {
+        const double th = remainder(6.28318530717958647693 * params[d] + (ls + lc), 6.28318530717958647693);
+        sth = sin(th);
+        cth = cos(th);
+    }
+    // per-item values (as the prep kernel computes them)
+    const int nitems = (int)P->items.size();
+    std::vector<SgItemVar> var(nitems);
+    for (int it = 0; it < nitems; it++) {
+        const SgItemRole &R = P->roles[it];
+        double sn = sth, cs = cth;
+        if (R.role != SG_ROLE_FORWARD && fam == 1) {
+            double tmp = sn;
+            sn = cs;
+            cs = -tmp;
+        }
+        double shift = R.role == SG_ROLE_ADJOINT ? phi_dev(fam, params[R.dir], params[d + R.dir], R.x) : 0.0;
+        if (fam == 1) {
+            var[it].sin_phi = sn * cos(shift) + cs * sin(shift);
+            var[it].cos_phi = cs * cos(shift) - sn * sin(shift);
+            var[it].base_rel = var[it].cos_phi;
+            var[it].mult = 1.0;
+        } else {
+            var[it].sin_phi = 0;
+            var[it].cos_phi = 1;
+            var[it].base_rel = 1;
+            var[it].mult = exp(shift);
+        }
+    }
+    std::vector<unsigned long long> B((size_t)SG_BINOM_K * (SG_MAX_D + 1));
+    sg_fill_binomials(B.data());
+
+    long long violations = 0, badpairs = 0;
+    unsigned long long evals = 0;
+    std::vector<double> slot(P->nchunks, 0.0);
+    int idx[SG_MAX_R];
+    for (unsigned long long c = 0; c < P->nchunks; c++) {
+        long long lo = 0, hi = (long long)P->pats.size() - 1;
+        while (lo < hi) {
+            long long mid = (lo + hi + 1) >> 1;
+            if (P->pat_chunk0[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const SgPatDev *Pp = &P->pats[lo];
+        const SgItemDev *I = &P->items[Pp->item];
+        if (c < I->chunk0 || c >= I->chunk0 + I->nchunk) violations++;
+        const SgItemVar &V = var[Pp->item];
+        const long long tbase = I->tab;
+        const int dd = I->d, r = Pp->r, skip = I->skip;
+        const unsigned long long rank = (c - Pp->chunk0) * Pp->spc;
+        unsigned long long cnt = Pp->nsub - rank < Pp->spc ? Pp->nsub - rank : Pp->spc;
+        sg_unrank_lex(rank, dd, r, B.data(), idx);
+        for (int t = 1; t < r; t++)
+            if (idx[t] <= idx[t - 1]) violations++;
+        if (idx[r - 1] >= dd) violations++;
+        auto check = [&](long long rel, long long blk_off, int m) {
+            const long long e = tbase + rel;
+            if (e < 0 || e >= P->nentries) {
+                violations++;
+                return false;
+            }
+            // must lie inside the intended block of this item's integral
+            const SgBlockDev &Bk = P->blocks[owner[e]];
+            if (Bk.off != tbase + blk_off || Bk.m != m) violations++;
+            return true;
+        };
+        double acc = 0.0;
+        while (cnt > 0) {
+            const int plast = idx[r - 1];
+            const int run = (unsigned long long)(dd - plast) < cnt ? dd - plast : (int)cnt;
+            const SgTailSegs seg = sg_tail_segments(Pp->toff, Pp->tm, plast, run, skip);
+            const int E = seg.E1 + seg.E2;
+            if (E != run * Pp->tm) violations++;
+            std::vector<double> S(Pp->A), W(Pp->A);
+            for (int a = 0; a < Pp->A; a++) {
+                int q = a;
+                double s = 0, w = 1;
+                for (int tt = r - 2; tt >= 0; tt--) {
+                    const int dir = sg_actual_dir(idx[tt], skip);
+                    if (dir == skip || dir >= dd + (skip >= 0)) violations++;
+                    const long long rel = sg_prefix_entry(Pp, tt, dir, &q);
+                    if (check(rel, Pp->poff[tt], Pp->pm[tt])) {
+                        s += tab[tbase + rel].x;
+                        w *= tab[tbase + rel].y;
+                    }
+                }
+                S[a] = s;
+                W[a] = w;
+            }
+            // replay the lane split of fold_run (one pass per prefix tile)
+            for (int ab = 0; ab < Pp->A; ab += SG_APAD) {
+                const int At = Pp->A - ab < SG_APAD ? Pp->A - ab : SG_APAD;
+                std::vector<int> seen((size_t)At * E, 0);
+                const int G = E >= 32 ? 1 : 32 / E, Eg = E >= 32 ? 32 : E;
+                for (int lane = 0; lane < 32; lane++) {
+                    const int sub = lane / Eg, el = lane - sub * Eg;
+                    if (sub >= G) continue;
+                    for (int e0 = 0; e0 < E; e0 += Eg) {
+                        const int e = e0 + el;
+                        if (e >= E) break;
+                        const long long rel = e < seg.E1 ? seg.base1 + e : seg.base2 + (e - seg.E1);
+                        if (!check(rel, Pp->toff, Pp->tm)) continue;
+                        const double2 te = tab[tbase + rel];
+                        for (int a = sub; a < At; a += G) {
+                            seen[(size_t)a * E + e]++;
+                            const double Sv = S[ab + a] + te.x, Wv = W[ab + a] * te.y;
+                            double D;
+                            if (I->gk == SG_GK_OSC) D = -2.0 * sin(0.5 * Sv) * (V.sin_phi * cos(0.5 * Sv) + V.cos_phi * sin(0.5 * Sv));
+                            else D = expm1(Sv);
+                            acc += Wv * D;
+                            evals++;
+                        }
+                    }
+                }
+                for (int v : seen)
+                    if (v != 1) badpairs++;
+            }
+            cnt -= run;
+            if (cnt > 0 && !sg_next_prefix(idx, dd, r)) violations++;
+        }
+        slot[c] = acc * Pp->coef;
+    }
+    // per-item fixed-order reduction and assembly
+    std::vector<double> vals(P->nout, 0.0);
+    long long nv = P->nv;
+    for (int it = 0; it < nitems; it++) {
+        const SgItemDev &I = P->items[it];
+        double s = 0, cc = 0;
+        for (unsigned long long q = 0; q < I.nchunk; q++) neu(s, cc, slot[I.chunk0 + q]);
+        const double rel = var[it].mult * (var[it].base_rel + (s + cc));
+        if (P->item_integral[it] < 0) {
+            if (vout && I.out < nv) vout[I.out] = rel;
+        } else {
+            vals[I.out] = rel;
+        }
+    }
+    out[0] = vals[0];
+    out[1] = ls + lc;
+    out[2] = (double)violations;
+    out[3] = (double)badpairs;
+    out[4] = (double)evals;
+    out[5] = (double)P->nchunks;
+    out[6] = (double)P->total_evals;
+    if (P->nout > 1) out[7] = vals[1];
+    if (nv_out) *nv_out = nv;
+    plan_free_host(P);
+    return 0;
+}
+}

@@ -1,0 +1,102 @@
+"""CPU tests of the library side: the C ABI loads and exports every function
+include/sg.h declares, and the planner + the fold kernel's enumeration
+primitives (replayed on the host by tests/index_check) stay inside their
+table blocks, visit every (prefix tuple, tail entry) pair once and give the
+oracle's value."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs as si
+import index_check
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "sg.h")).read()
+    return sorted(set(re.findall(r"SG_API\s+[\w\s\*]+?\b(sg_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    import paper_2210_14313_gb300 as sg
+    lib = sg.load()
+    declared = _header_functions()
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(sg.ABI_SYMBOLS) == declared
+
+
+def test_status_strings():
+    import paper_2210_14313_gb300 as sg
+    lib = sg.load()
+    for code in range(7):
+        assert lib.sg_status_string(code)
+    assert b"unknown" in lib.sg_status_string(99)
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    # NULL handles / out pointers are rejected before any CUDA call
+    import ctypes
+    import paper_2210_14313_gb300 as sg
+    lib = sg.load()
+    assert lib.sg_rule_init(3, 4, ctypes.byref(ctypes.c_void_p())) == 1       # bad rule kind
+    assert lib.sg_rule_init(2, 0, ctypes.byref(ctypes.c_void_p())) == 2       # level out of range
+    assert lib.sg_rule_init(2, 4, None) == 1
+    assert lib.sg_integrate(None, 0, None, 0, 4, 9, 0, 0, None, None) == 1
+    r = sg.sg_result()
+    assert lib.sg_integrate(None, 0, ctypes.c_void_p(1), 0, 4, 9, 0, 0, None, ctypes.byref(r)) == 1
+    t = sg.sg_tuning(10, 8, 8)
+    assert lib.sg_set_tuning(1, ctypes.byref(t)) == 2
+    assert lib.sg_get_tuning(7, ctypes.byref(t)) == 1
+
+
+def _oracle_rel(c, r):
+    o = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
+    if c["fam"] == si.FAM_OSCILLATORY:
+        return abs(r["rel"] - o.value) / abs(o.value)
+    q = r["rel"] * math.exp(r["logscale"] - o.exp2 * math.log(2.0))
+    return abs(q - o.mant) / abs(o.mant)
+
+
+CASES = [si.cfg1(), si.cfg2(), si.cfg3(si.FAM_PRODUCT_PEAK), si.cfg3(si.FAM_GAUSSIAN)]
+CASES += [dict(name="ragged%d" % k, **it) for k, it in enumerate(si.batch(n=8, seed=3, d_hi=30, L_hi=4))]
+CASES += [dict(name="d1", rule=2, fam=3, d=1, L=6, params=si.item_params(3, 1, 5)),
+          dict(name="L0", rule=4, fam=1, d=7, L=0, params=si.item_params(1, 7, 6)),
+          dict(name="d_lt_L", rule=4, fam=2, d=2, L=6, params=si.item_params(2, 2, 7)),
+          dict(name="trap", rule=1, fam=0, d=5, L=4, params=si.item_params(0, 5, 8))]
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c["name"])
+def test_fold_enumeration_matches_oracle(case, form):
+    r = index_check.run(case["rule"], case["fam"], case["params"], case["d"], case["L"], form=form)
+    assert r["violations"] == 0
+    assert r["badpairs"] == 0
+    assert r["evals"] == r["plan_evals"]
+    tol = 1e-12 if form != 3 else 1e-11
+    assert _oracle_rel(case, r) < tol
+
+
+@pytest.mark.parametrize("ppc,ctas,warps", [(64, 1, 1), (100, 3, 2), (1 << 20, 8, 8)])
+def test_chunking_does_not_change_the_sum(ppc, ctas, warps):
+    c = si.cfg2()
+    r = index_check.run(c["rule"], c["fam"], c["params"], c["d"], c["L"], form=2, ppc=ppc,
+                        ctas_per_sm=ctas, warps=warps)
+    assert r["violations"] == 0 and r["badpairs"] == 0
+    assert _oracle_rel(c, r) < 1e-12
+
+
+def test_n_d_q_matches_oracle_count():
+    # the combination form evaluates exactly the points of Eq. 2.6's tensor
+    # grids, except the all-centre point when that subgrid belongs to the rule
+    # (d > L), whose deviation is zero by construction
+    for c in CASES:
+        r = index_check.run(c["rule"], c["fam"], c["params"], c["d"], c["L"], form=3)
+        centre = 1 if c["d"] > c["L"] else 0
+        assert r["evals"] == oracle.count_points(c["rule"], c["d"], c["L"]) - centre

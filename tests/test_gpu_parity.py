@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars: FP64 relative error <= 1e-12; the mixed path (float evaluation and
+folds, double combination) <= 1e-6 where its own error estimate says the
+integrand is conditioned well enough (see test_mixed_guard for the rest).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs as si
+import dp_pin
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2210_14313_gb300 as sg  # noqa: E402
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def rules():
+    return {k: sg.Rule(k, max_level=10) for k in (1, 2, 4)}
+
+
+def rel_err(r, o):
+    """Relative error of a GPU Result against an oracle Result (mant, exp2)."""
+    return abs(r.mant * 2.0 ** (r.exp2 - o.exp2) - o.mant) / abs(o.mant)
+
+
+_ORACLE = {}
+
+
+def oracle_value(c):
+    key = (c["rule"], c["fam"], c["d"], c["L"], tuple(np.asarray(c["params"]).tolist()))
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
+    return _ORACLE[key]
+
+
+CONFIGS = [si.cfg1(), si.cfg2(), si.cfg3(si.FAM_PRODUCT_PEAK), si.cfg3(si.FAM_GAUSSIAN), si.cfg5()]
+
+
+@pytest.mark.parametrize("form", [sg.FORM_TELESCOPED, sg.FORM_DIFFERENCE])
+@pytest.mark.parametrize("c", CONFIGS, ids=lambda c: c["name"])
+def test_fp64_configs(rules, c, form):
+    r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"],
+                     prec=sg.PREC_FP64, form=form)
+    assert r.points == oracle.count_points(c["rule"], c["d"], c["L"])
+    assert rel_err(r, oracle_value(c)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("c", [si.cfg1(), si.cfg2()], ids=lambda c: c["name"])
+def test_fp64_combination_form(rules, c):
+    # Eq. 2.6 literally; its binomial coefficients amplify rounding by the
+    # conditioning of the combination, so the bar is scaled by it
+    r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"],
+                     prec=sg.PREC_FP64, form=sg.FORM_COMBINATION)
+    assert rel_err(r, oracle_value(c)) <= max(FP64_TOL, 1e-15 * r.cond)
+
+
+@pytest.mark.parametrize("c", [si.cfg3(si.FAM_PRODUCT_PEAK), si.cfg3(si.FAM_GAUSSIAN), si.cfg5(),
+                               si.cfg1()], ids=lambda c: c["name"])
+def test_mixed_configs(rules, c):
+    r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"],
+                     prec=sg.PREC_MIXED)
+    err = rel_err(r, oracle_value(c))
+    assert err <= MIXED_TOL, (err, r)
+    assert err <= max(20 * r.err_est, 1e-7)  # the estimate is of the right size
+
+
+EDGE = [dict(name="d1_L6", rule=2, fam=3, d=1, L=6, params=si.item_params(3, 1, 5)),
+        dict(name="L0", rule=4, fam=1, d=7, L=0, params=si.item_params(1, 7, 6)),
+        dict(name="L1", rule=2, fam=2, d=33, L=1, params=si.item_params(2, 33, 9)),
+        dict(name="d_lt_L", rule=4, fam=2, d=2, L=6, params=si.item_params(2, 2, 7)),
+        dict(name="trapezoid", rule=1, fam=0, d=5, L=4, params=si.item_params(0, 5, 8)),
+        dict(name="gl_deep", rule=4, fam=3, d=6, L=8, params=si.item_params(3, 6, 10)),
+        dict(name="peak_d200_underflow", rule=2, fam=2, d=200, L=2,
+             params=si.item_params(2, 200, 1234))]
+EDGE += [dict(name="ragged%d" % k, **it) for k, it in enumerate(si.batch(n=10, seed=3, d_hi=40, L_hi=4))]
+
+
+@pytest.mark.parametrize("c", EDGE, ids=lambda c: c["name"])
+def test_fp64_edge_and_ragged(rules, c):
+    r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"],
+                     prec=sg.PREC_FP64)
+    assert rel_err(r, oracle_value(c)) <= FP64_TOL
+
+
+def test_fp64_is_bitwise_deterministic(rules):
+    c = si.cfg2()
+    a = sg.integrate(rules[4], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=sg.PREC_FP64)
+    b = sg.integrate(rules[4], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=sg.PREC_FP64)
+    assert a.mant == b.mant and a.exp2 == b.exp2
+    c = si.cfg3(si.FAM_GAUSSIAN)
+    a = sg.integrate(rules[2], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=sg.PREC_MIXED)
+    b = sg.integrate(rules[2], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=sg.PREC_MIXED)
+    assert a.mant == b.mant and a.exp2 == b.exp2
+
+
+def test_tuning_changes_only_rounding(rules):
+    c = si.cfg2()
+    saved = sg.get_tuning(sg.PREC_FP64)
+    try:
+        vals = []
+        for t in [(64, 1, 1), (512, 4, 4), (1 << 20, 16, 8)]:
+            sg.set_tuning(sg.PREC_FP64, *t)
+            r = sg.integrate(rules[4], c["fam"], c["params"], c["d"], c["d"] + c["L"])
+            assert rel_err(r, oracle_value(c)) <= FP64_TOL
+            vals.append(r.mant)
+    finally:
+        sg.set_tuning(sg.PREC_FP64, *saved)
+
+
+def test_async_matches_blocking(rules):
+    c = si.cfg2()
+    q = c["d"] + c["L"]
+    dp = torch.tensor(c["params"], dtype=torch.float64, device="cuda")
+    out = torch.zeros(sg.DEV_RESULT_DOUBLES, dtype=torch.float64, device="cuda")
+    sg.integrate_async(rules[4], c["fam"], dp, c["d"], q, out)
+    torch.cuda.synchronize()
+    r = sg.integrate(rules[4], c["fam"], c["params"], c["d"], q)
+    assert out[0].item() == r.mant and int(out[1].item()) == r.exp2
+
+
+def test_invalid_arguments_return_status(rules):
+    lib = sg.load()
+    import ctypes
+    res = sg.sg_result()
+    p = np.zeros(8)
+    ptr = ctypes.c_void_p(p.ctypes.data)
+    s = sg._stream_handle()
+    assert lib.sg_integrate(rules[2].handle, 0, ptr, 0, 4, 3, 0, 0, s, ctypes.byref(res)) == 1   # q < d
+    assert lib.sg_integrate(rules[2].handle, 9, ptr, 0, 4, 5, 0, 0, s, ctypes.byref(res)) == 1   # family
+    assert lib.sg_integrate(rules[2].handle, 0, ptr, 0, 4, 4 + 10, 0, 0, s, ctypes.byref(res)) == 2  # level
+    assert lib.sg_integrate(rules[2].handle, 0, ptr, 0, 9000, 9001, 0, 0, s, ctypes.byref(res)) == 2  # d
+    with pytest.raises(sg.SgError):
+        sg.integrate(rules[2], 0, p, 4, 3)
+
+
+# ---------------------------------------------------------------------------
+# batch
+# ---------------------------------------------------------------------------
+
+def _batch(items, rules):
+    specs, pool, off = [], [], 0
+    for it in items:
+        specs.append((rules[it["rule"]], it["fam"], it["d"], it["d"] + it["L"], off))
+        pool.append(np.asarray(it["params"]))
+        off += 2 * it["d"]
+    return specs, np.concatenate(pool)
+
+
+def test_batch_fp64_matches_oracle(rules):
+    items = si.batch(n=48, seed=11, d_hi=40, L_hi=4)
+    specs, pool = _batch(items, rules)
+    res = sg.integrate_batch(specs, pool, prec=sg.PREC_FP64)
+    for it, r in zip(items, res):
+        assert rel_err(r, oracle_value(it)) <= FP64_TOL
+    # a second replay of the cached graph gives the same bits
+    res2 = sg.integrate_batch(specs, pool, prec=sg.PREC_FP64)
+    assert all(a.mant == b.mant for a, b in zip(res, res2))
+
+
+def test_batch_matches_single_calls(rules):
+    items = si.batch(n=16, seed=12, d_hi=60, L_hi=4)
+    specs, pool = _batch(items, rules)
+    res = sg.integrate_batch(specs, pool, prec=sg.PREC_FP64)
+    for it, r in zip(items, res):
+        s = sg.integrate(rules[it["rule"]], it["fam"], it["params"], it["d"], it["d"] + it["L"])
+        assert abs(r.mant * 2.0 ** (r.exp2 - s.exp2) - s.mant) <= 1e-13 * abs(s.mant)
+
+
+def test_mixed_guard(rules):
+    # without the guard, badly conditioned items miss 1e-6 in float; with
+    # it every item is within 1e-6 of the oracle
+    items = si.batch(n=48, seed=13, d_hi=40, L_hi=4)
+    specs, pool = _batch(items, rules)
+    res = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED, guard_tol=MIXED_TOL / 4)
+    for it, r in zip(items, res):
+        assert rel_err(r, oracle_value(it)) <= MIXED_TOL
+    raw = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED, guard_tol=0.0)
+    for it, r in zip(items, raw):
+        err = rel_err(r, oracle_value(it))
+        if r.err_est <= MIXED_TOL / 4:
+            assert err <= MIXED_TOL
+
+
+def test_batch_full_size_sampled(rules):
+    """The full 4096-item workload in one launch (mixed, guarded); every item
+    against the float64 separable DP, the small ones also against the oracle."""
+    items = si.batch()
+    specs, pool = _batch(items, rules)
+    res = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED, guard_tol=MIXED_TOL / 4)
+    worst = 0.0
+    checked = 0
+    for it, r in zip(items, res):
+        rel, ls = dp_pin.smolyak_value_f64(it["rule"], it["fam"], it["params"], it["d"], it["L"])
+        if it["fam"] == si.FAM_OSCILLATORY:
+            ref, got = rel, r.value
+        else:
+            ref = rel
+            got = r.mant * math.exp(r.exp2 * math.log(2.0) - ls)
+        worst = max(worst, abs(got - ref) / abs(ref))
+        if r.points <= 2e5 and checked < 64:
+            assert rel_err(r, oracle_value(it)) <= MIXED_TOL
+            checked += 1
+    assert worst <= MIXED_TOL, worst
+    assert checked >= 16
+
+
+# ---------------------------------------------------------------------------
+# gradient
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fam", [0, 1, 2, 3, 4])
+def test_grad_small_all_families(rules, fam):
+    kind, d, L = (4, 7, 3) if fam % 2 else (2, 9, 3)
+    p = si.item_params(fam, d, 77 + fam)
+    r, g = sg.integrate_grad(rules[kind], fam, p, d, d + L)
+    o, go = oracle.gradient(kind, fam, p, d, L, list(range(2 * d)))
+    go = np.ldexp(go, o.exp2)
+    assert rel_err(r, o) <= FP64_TOL
+    assert np.abs(g - go).max() <= FP64_TOL * np.abs(go).max()
+
+
+def test_grad_cfg5_matches_oracle_subset_and_fd(rules):
+    c = si.cfg5()
+    q = c["d"] + c["L"]
+    r, g = sg.integrate_grad(rules[2], c["fam"], c["params"], c["d"], q)
+    idx = dp_pin.sample_idx(c["d"])
+    o, go = oracle.gradient(c["rule"], c["fam"], c["params"], c["d"], c["L"], idx)
+    go = np.ldexp(go, o.exp2)
+    assert np.abs(g[idx] - go).max() <= FP64_TOL * np.abs(go).max()
+    # central differences of the GPU value itself
+    p = np.asarray(c["params"])
+    for j in idx[:6]:
+        h = 1e-5 * max(abs(p[j]), 1e-3)
+        pp, pm = p.copy(), p.copy()
+        pp[j] += h
+        pm[j] -= h
+        fd = (sg.integrate(rules[2], c["fam"], pp, c["d"], q).value -
+              sg.integrate(rules[2], c["fam"], pm, c["d"], q).value) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-6 * np.abs(g).max()
+    # mixed-precision adjoint
+    rm, gm = sg.integrate_grad(rules[2], c["fam"], c["params"], c["d"], q, prec=sg.PREC_MIXED)
+    assert np.abs(gm - g).max() <= MIXED_TOL * np.abs(g).max()
+
+
+def test_autograd_function(rules):
+    c = si.cfg5()
+    q = c["d"] + c["L"]
+    p = torch.tensor(c["params"], dtype=torch.float64, device="cuda", requires_grad=True)
+    val = sg.sg_quad(p, rules[2], c["fam"], c["d"], q)
+    (3.0 * val).backward()
+    _, g = sg.integrate_grad(rules[2], c["fam"], c["params"], c["d"], q)
+    assert torch.allclose(p.grad.cpu(), torch.tensor(3.0 * g), rtol=0, atol=1e-15 * np.abs(g).max())
