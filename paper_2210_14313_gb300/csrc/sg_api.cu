@@ -50,7 +50,23 @@ static std::mutex g_mu;
 struct DevCtx {
     int sms = 0;
     u64 *binom = nullptr;
+    std::map<std::pair<int, int>, int> occ;  // (prec, warps per CTA) -> resident CTAs per SM
 };
+
+static int dev_occupancy(DevCtx *C, int prec, int warps) {
+    auto key = std::make_pair(prec, warps);
+    auto it = C->occ.find(key);
+    if (it != C->occ.end()) return it->second;
+    int n = sg_fold_occupancy(prec, 0, warps);
+    if (n < 1) n = 1;
+    C->occ[key] = n;
+    return n;
+}
+
+static long long resident_warps(DevCtx *C, int prec, const sg_tuning &t) {
+    const int per_sm = std::max(1, std::min(dev_occupancy(C, prec, t.warps_per_cta), t.ctas_per_sm));
+    return (long long)C->sms * per_sm * t.warps_per_cta;
+}
 static std::map<int, DevCtx> g_dev;
 
 static sg_status dev_ctx(DevCtx **out) {
@@ -230,10 +246,10 @@ static sg_status plan_upload(Plan *P) {
     return SG_OK;
 }
 
-static sg_status build_plan(const std::vector<Req> &reqs, int prec, const sg_tuning &tune, int sms,
-                            Plan **out) {
+static sg_status build_plan(const std::vector<Req> &reqs, int prec, const sg_tuning &tune,
+                            long long warps, Plan **out) {
     Plan *P = nullptr;
-    sg_status st = build_plan_host(reqs, prec, tune, sms, &P);
+    sg_status st = build_plan_host(reqs, prec, tune, warps, &P);
     if (st != SG_OK) return st;
     st = plan_upload(P);
     if (st != SG_OK) {
@@ -301,7 +317,7 @@ static sg_status get_plan(const std::vector<Req> &reqs, int prec, Plan **out) {
         return SG_OK;
     }
     Plan *P = nullptr;
-    st = build_plan(reqs, prec, k.t, C->sms, &P);
+    st = build_plan(reqs, prec, k.t, resident_warps(C, prec, k.t), &P);
     if (st != SG_OK) return st;
     if (g_plans.size() > 256) {  // bound the cache
         cudaDeviceSynchronize();
@@ -330,10 +346,11 @@ struct GraphEntry {
 struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
-    DevBuf tab32, tab64, slots, counters, flags, bases, vars, out, vout, grad, params;
+    DevBuf tab32, tab64, slots, gslots, counters, flags, bases, vars, out, vout, grad, params;
     void *h_pinned = nullptr;
     size_t h_cap = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_join = nullptr;
+    cudaStream_t own = nullptr;  // capture/replay stream of batch graphs (never the legacy stream)
     unsigned epoch = 0;
     std::map<std::tuple<const Plan *, const double *, double, unsigned>, GraphEntry> graphs;
     // fold-kernel timing (sg_profile_begin / sg_profile_end)
@@ -343,7 +360,7 @@ struct Workspace {
 };
 
 // Records an event pair around a fold launch when profiling is on.
-static cudaError_t prof_mark(Workspace *W, bool start) {
+static cudaError_t prof_mark(Workspace *W, bool start, cudaStream_t s) {
     if (!W->profiling) return cudaSuccess;
     if (start) {
         if (W->prof_used == W->prof.size()) {
@@ -353,9 +370,9 @@ static cudaError_t prof_mark(Workspace *W, bool start) {
             if (e != cudaSuccess) return e;
             W->prof.push_back(ev);
         }
-        return cudaEventRecord(W->prof[W->prof_used].first, W->stream);
+        return cudaEventRecord(W->prof[W->prof_used].first, s);
     }
-    return cudaEventRecord(W->prof[W->prof_used++].second, W->stream);
+    return cudaEventRecord(W->prof[W->prof_used++].second, s);
 }
 static std::map<std::pair<int, cudaStream_t>, Workspace *> g_ws;
 
@@ -379,7 +396,9 @@ static sg_status get_ws(cudaStream_t s, Workspace **out) {
     Workspace *W = new Workspace();
     W->device = dev;
     W->stream = s;
-    if (cudaEventCreate(&W->ev0) != cudaSuccess || cudaEventCreate(&W->ev1) != cudaSuccess) {
+    if (cudaEventCreate(&W->ev0) != cudaSuccess || cudaEventCreate(&W->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&W->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&W->own, cudaStreamNonBlocking) != cudaSuccess) {
         delete W;
         return SG_ECUDA;
     }
@@ -392,6 +411,7 @@ static sg_status ensure(Workspace *W, DevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.p && b.cap >= bytes) return SG_OK;
     cudaStreamSynchronize(W->stream);
+    if (W->own) cudaStreamSynchronize(W->own);
     drop_graphs(W);
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
@@ -430,13 +450,17 @@ static sg_status ensure_host(Workspace *W, size_t bytes) {
         if (s_ != SG_OK) return s_;      \
     } while (0)
 
+// Counters: [u64 work][u32 item tickets][u32 group tickets], zeroed per launch.
+static size_t counter_bytes(const Plan *P) { return 16 + 4 * (P->items.size() + P->ngroups); }
+
 // Makes every buffer a plan needs large enough (outside any capture).
 static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need64,
                             size_t param_doubles) {
     if (need32) ST(ensure(W, W->tab32, (size_t)P->nentries * sizeof(float2)));
     if (need64) ST(ensure(W, W->tab64, (size_t)P->nentries * sizeof(double2)));
     ST(ensure(W, W->slots, (size_t)P->nchunks * sizeof(SgSlot)));
-    ST(ensure(W, W->counters, 16 + 4 * P->items.size()));
+    ST(ensure(W, W->gslots, (size_t)P->ngroups * sizeof(SgGroupSlot)));
+    ST(ensure(W, W->counters, counter_bytes(P)));
     ST(ensure(W, W->flags, 4 * P->items.size()));
     ST(ensure(W, W->bases, P->integrals.size() * sizeof(SgBaseDev)));
     ST(ensure(W, W->vars, P->items.size() * sizeof(SgItemVar)));
@@ -447,12 +471,12 @@ static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need6
     return SG_OK;
 }
 
-static SgLaunchCfg fold_cfg(const Plan *P, int prec, int sms) {
+static SgLaunchCfg fold_cfg(const Plan *P, int prec, DevCtx *C) {
     SgLaunchCfg c;
     c.warps_per_cta = P->tune.warps_per_cta;
-    int occ = sg_fold_occupancy(prec, 0, c.warps_per_cta);
+    int occ = dev_occupancy(C, prec, c.warps_per_cta);
     int per_sm = std::max(1, std::min(occ, P->tune.ctas_per_sm));
-    long long ctas = (long long)sms * per_sm;
+    long long ctas = (long long)C->sms * per_sm;
     const long long need = (long long)((P->nchunks + c.warps_per_cta - 1) / c.warps_per_cta);
     if (need < ctas) ctas = std::max<long long>(need, 1);
     c.ctas = (int)ctas;
@@ -461,13 +485,12 @@ static SgLaunchCfg fold_cfg(const Plan *P, int prec, int sms) {
 
 // Enqueues the whole computation of a plan on W->stream (capturable: no
 // allocation, no synchronisation).  prec_run: 0 FP64, 1 mixed.
-static sg_status run_plan(const Plan *P, Workspace *W, const DevCtx *C, const double *d_params,
-                          double guard_tol, SgOutDev *d_out) {
-    cudaStream_t s = W->stream;
+static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *d_params,
+                          double guard_tol, SgOutDev *d_out, cudaStream_t s) {
     const int prec = P->prec;
     const int nitems = (int)P->items.size();
     SgOutDev *outp = d_out ? d_out : (SgOutDev *)W->out.p;
-    CK(cudaMemsetAsync(W->counters.p, 0, 16 + 4 * (size_t)nitems, s));
+    CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
     if (guard_tol > 0.0) CK(cudaMemsetAsync(W->flags.p, 0, 4 * (size_t)nitems, s));
     SgSetupArgs sa;
     memset(&sa, 0, sizeof(sa));
@@ -513,6 +536,8 @@ static sg_status run_plan(const Plan *P, Workspace *W, const DevCtx *C, const do
     fa.slots = (SgSlot *)W->slots.p;
     fa.work = (unsigned long long *)W->counters.p;
     fa.item_done = (unsigned int *)((char *)W->counters.p + 16);
+    fa.gslots = (SgGroupSlot *)W->gslots.p;
+    fa.group_done = fa.item_done + nitems;
     fa.bases = (SgBaseDev *)W->bases.p;
     fa.item_integral = P->d_item_integral;
     fa.out = outp;
@@ -521,12 +546,12 @@ static sg_status run_plan(const Plan *P, Workspace *W, const DevCtx *C, const do
     fa.skip_unflagged = nullptr;
     fa.guard_tol = guard_tol;
     fa.unit_roundoff = u;
-    CK(prof_mark(W, true));
-    CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C->sms), s));
-    CK(prof_mark(W, false));
+    CK(prof_mark(W, true, s));
+    CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
+    CK(prof_mark(W, false, s));
     if (prec == 1 && guard_tol > 0.0) {
         // precision guard: recompute flagged items in FP64
-        CK(cudaMemsetAsync(W->counters.p, 0, 16 + 4 * (size_t)nitems, s));
+        CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
         sa.tab32 = nullptr;
         sa.tab64 = (double2 *)W->tab64.p;
         sa.flags = (int *)W->flags.p;
@@ -535,9 +560,9 @@ static sg_status run_plan(const Plan *P, Workspace *W, const DevCtx *C, const do
         fa.skip_unflagged = (int *)W->flags.p;
         fa.guard_tol = 0.0;
         fa.unit_roundoff = 1.1102230246251565e-16;
-        CK(prof_mark(W, true));
-        CK(sg_launch_fold(fa, 0, 0, fold_cfg(P, 0, C->sms), s));
-        CK(prof_mark(W, false));
+        CK(prof_mark(W, true, s));
+        CK(sg_launch_fold(fa, 0, 0, fold_cfg(P, 0, C), s));
+        CK(prof_mark(W, false, s));
     }
     return SG_OK;
 }
@@ -608,6 +633,7 @@ extern "C" sg_status sg_integrate_async(sg_rule rule, sg_family fam, const doubl
     if (!d_params || !d_out) return SG_EINVAL;
     ST(check_one(rule, fam, d, q, prec, &form));
     std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();  // a failed earlier call must not surface here
     DevCtx *C = nullptr;
     ST(dev_ctx(&C));
     Plan *P = nullptr;
@@ -618,7 +644,7 @@ extern "C" sg_status sg_integrate_async(sg_rule rule, sg_family fam, const doubl
     Workspace *W = nullptr;
     ST(get_ws((cudaStream_t)stream, &W));
     ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, 0));
-    return run_plan(P, W, C, d_params, 0.0, (SgOutDev *)d_out);
+    return run_plan(P, W, C, d_params, 0.0, (SgOutDev *)d_out, (cudaStream_t)stream);
 }
 
 extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *params,
@@ -627,6 +653,7 @@ extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *par
     if (!params || !out) return SG_EINVAL;
     ST(check_one(rule, fam, d, q, prec, &form));
     std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();  // a failed earlier call must not surface here
     DevCtx *C = nullptr;
     ST(dev_ctx(&C));
     Plan *P = nullptr;
@@ -645,7 +672,7 @@ extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *par
         dp = (const double *)W->params.p;
     }
     CK(cudaEventRecord(W->ev0, s));
-    ST(run_plan(P, W, C, dp, 0.0, nullptr));
+    ST(run_plan(P, W, C, dp, 0.0, nullptr, s));
     CK(cudaEventRecord(W->ev1, s));
     CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -683,6 +710,7 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     size_t pool = 0;
     ST(batch_reqs(items, n, reqs, &pool));
     std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();  // a failed earlier call must not surface here
     DevCtx *C = nullptr;
     ST(dev_ctx(&C));
     Plan *P = nullptr;
@@ -693,9 +721,13 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     const bool guard = prec == SG_PREC_MIXED && guard_tol > 0.0;
     ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64 || guard, params_on_device ? 0 : pool));
     ST(ensure_host(W, (size_t)P->nout * sizeof(SgOutDev)));
+    // graphs run on the workspace's own stream, ordered after the caller's work
+    cudaStream_t g = W->own;
+    CK(cudaEventRecord(W->ev_join, s));
+    CK(cudaStreamWaitEvent(g, W->ev_join, 0));
     const double *dp = params_pool;
     if (!params_on_device) {
-        CK(cudaMemcpyAsync(W->params.p, params_pool, pool * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(W->params.p, params_pool, pool * sizeof(double), cudaMemcpyHostToDevice, g));
         dp = (const double *)W->params.p;
     }
     // the launch sequence is captured once per (plan, params, guard) and replayed
@@ -703,22 +735,27 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     auto it = W->graphs.find(key);
     if (it == W->graphs.end()) {
         GraphEntry ge;
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        sg_status st = run_plan(P, W, C, dp, guard_tol, nullptr);
-        cudaError_t ce = cudaStreamEndCapture(s, &ge.g);
-        if (st != SG_OK) return st;
+        CK(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
+        sg_status st = run_plan(P, W, C, dp, guard_tol, nullptr, g);
+        cudaError_t ce = cudaStreamEndCapture(g, &ge.g);
+        if (st != SG_OK) {
+            if (ge.g) cudaGraphDestroy(ge.g);
+            cudaGetLastError();
+            return st;
+        }
         if (ce != cudaSuccess) return SG_ECUDA;
         if (cudaGraphInstantiate(&ge.x, ge.g, 0) != cudaSuccess) {
             cudaGraphDestroy(ge.g);
+            cudaGetLastError();
             return SG_ECUDA;
         }
         it = W->graphs.emplace(key, ge).first;
     }
-    CK(cudaEventRecord(W->ev0, s));
-    CK(cudaGraphLaunch(it->second.x, s));
-    CK(cudaEventRecord(W->ev1, s));
-    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, (size_t)n * sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(cudaEventRecord(W->ev0, g));
+    CK(cudaGraphLaunch(it->second.x, g));
+    CK(cudaEventRecord(W->ev1, g));
+    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, (size_t)n * sizeof(SgOutDev), cudaMemcpyDeviceToHost, g));
+    CK(cudaStreamSynchronize(g));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, W->ev0, W->ev1);
     const SgOutDev *o = (const SgOutDev *)W->h_pinned;
@@ -734,6 +771,7 @@ extern "C" sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double
     sg_form form = SG_FORM_AUTO;
     ST(check_one(rule, fam, d, q, prec, &form));
     std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();  // a failed earlier call must not surface here
     DevCtx *C = nullptr;
     ST(dev_ctx(&C));
     Plan *P = nullptr;
@@ -752,7 +790,7 @@ extern "C" sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double
         dp = (const double *)W->params.p;
     }
     CK(cudaEventRecord(W->ev0, s));
-    ST(run_plan(P, W, C, dp, 0.0, nullptr));
+    ST(run_plan(P, W, C, dp, 0.0, nullptr, s));
     SgGradArgs ga;
     ga.fam = (int)fam;
     ga.d = d;
@@ -870,6 +908,7 @@ extern "C" sg_status sg_ceiling(sg_precision prec, int kind, void *stream, doubl
     if (!rate || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) || kind < 0 || kind > 2)
         return SG_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();  // a failed earlier call must not surface here
     DevCtx *C = nullptr;
     ST(dev_ctx(&C));
     Workspace *W = nullptr;

@@ -43,6 +43,8 @@ struct SgItemDev {
     int pad;
     unsigned long long chunk0;  // first chunk of the item
     unsigned long long nchunk;  // chunks of the item
+    unsigned long long group0;  // first reduction group of the item (SG_GROUP chunks each)
+    unsigned long long ngroups; // reduction groups of the item
 };
 
 // Role of an item, from which the per-call values below are derived once
@@ -80,8 +82,18 @@ struct SgPatDev {
     unsigned long long chunk0; // first global chunk of this pattern
 };
 
+// Chunks per reduction group: the warp that completes the last chunk of a
+// group sums the group's slots; the warp that completes the last group of an
+// item sums the group results.  Both sums run in a fixed order.
+#define SG_GROUP 64
+
+// Per-group partial result: compensated pair and absolute sum.
+struct alignas(32) SgGroupSlot {
+    double s, c, abs, pad;
+};
+
 // Per-chunk partial result (written once by the warp that ran the chunk).
-struct SgSlot {
+struct alignas(16) SgSlot {
     double sum;
     double abs;
 };

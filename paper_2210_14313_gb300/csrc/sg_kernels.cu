@@ -113,11 +113,37 @@ template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double S, 
 // when the enumerated directions jump over a left-out direction).  Lanes are
 // spread over tail entries; when a run has fewer than 32 entries, the warp
 // splits into groups that take different prefix tuples.
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// Per-lane accumulators of a fold: a double for the FP64 path; for the mixed
+// path a float pair (running sum + TwoSum error term) fed with plain float
+// partial sums of 8 points, so that no double-precision instruction sits in
+// the inner loop (GB300 runs FP64 at 1/64 of the FP32 rate).
+struct FoldAcc {
+    double acc = 0.0;
+    float hs = 0.f, hc = 0.f, habs = 0.f;
+};
+
+// Prefix state of one prefix node tuple: partial argument S and weight W.
+template <typename T> struct PrefixState;
+template <> struct PrefixState<float> { typedef float2 type; };
+template <> struct PrefixState<double> { typedef double2 type; };
+
+// Folds the points (prefix tuple a < At) x (tail entries e < E1 + E2) of one
+// run.  Tail entries come from up to two contiguous table segments (two
+// when the enumerated directions jump over a left-out direction).  Lanes are
+// spread over tail entries; when a run has fewer than 32 entries, the warp
+// splits into groups that take different prefix tuples.
 template <typename T, int GK>
 __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict__ tab,
                                          long long base1, int E1, long long base2, int E2,
-                                         const T *sS, const T *sW, int At, T sphi, T cphi, int lane,
-                                         double &acc, double &aabs) {
+                                         const typename PrefixState<T>::type *sP, int At, T sphi,
+                                         T cphi, int lane, FoldAcc &F) {
     typedef typename V2T<T>::type V2;
     const int E = E1 + E2;
     const int G = E >= 32 ? 1 : 32 / E;
@@ -129,41 +155,51 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
         if (e >= E) break;
         const V2 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
         if constexpr (sizeof(T) == 4) {
-            // float folds, flushed into the double accumulators every 8 points
-            float part = 0.f, pabs = 0.f;
-            int n = 0;
-            for (int a = sub; a < At; a += G) {
-                const float S = sS[a] + te.x;
-                const float W = sW[a] * te.y;
-                const float D = gdev<float, GK>(S, sphi, cphi);
-                part = fmaf(W, D, part);
-                pabs = fmaf(fabsf(W), fabsf(D), pabs);
-                if (++n == 8) {
-                    acc += (double)part;
-                    aabs += (double)pabs;
-                    part = 0.f;
-                    pabs = 0.f;
-                    n = 0;
+            float hs = F.hs, hc = F.hc, habs = F.habs;
+            int a = sub;
+            for (; a + 7 * G < At; a += 8 * G) {
+                float part = 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float2 p = sP[a + u * G];
+                    const float W = p.y * te.y;
+                    const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
+                    part = fmaf(W, D, part);
+                    habs = fmaf(fabsf(W), fabsf(D), habs);
                 }
+                float t, err;
+                two_sum(hs, part, t, err);
+                hs = t;
+                hc += err;
             }
-            acc += (double)part;
-            aabs += (double)pabs;
+            float part = 0.f;
+            for (; a < At; a += G) {
+                const float2 p = sP[a];
+                const float W = p.y * te.y;
+                const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
+                part = fmaf(W, D, part);
+                habs = fmaf(fabsf(W), fabsf(D), habs);
+            }
+            float t, err;
+            two_sum(hs, part, t, err);
+            F.hs = t;
+            F.hc = hc + err;
+            F.habs = habs;
         } else {
+            double acc = F.acc;
             for (int a = sub; a < At; a += G) {
-                const double S = sS[a] + te.x;
-                const double W = sW[a] * te.y;
-                const double D = gdev<double, GK>(S, sphi, cphi);
-                acc = fma(W, D, acc);
-                aabs = fma(fabs(W), fabs(D), aabs);
+                const double2 p = sP[a];
+                acc = fma(p.y * te.y, gdev<double, GK>(p.x + te.x, sphi, cphi), acc);
             }
+            F.acc = acc;
         }
     }
 }
 
 template <typename T, int GK>
 __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
-                           const SgItemDev *__restrict__ I, unsigned long long c, T *sS, T *sW,
-                           int *sIdx, int lane, double &acc, double &aabs) {
+                           const SgItemDev *__restrict__ I, unsigned long long c,
+                           typename PrefixState<T>::type *sP, int *sIdx, int lane, FoldAcc &F) {
     typedef typename V2T<T>::type V2;
     const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
     const int d = I->d, r = P->r, skip = I->skip, Atot = P->A, tm = P->tm;
@@ -188,12 +224,11 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                     S += e.x;
                     W *= e.y;
                 }
-                sS[a] = S;
-                sW[a] = W;
+                sP[a].x = S;
+                sP[a].y = W;
             }
             __syncwarp();
-            fold_run<T, GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sS, sW, At, sphi, cphi, lane,
-                            acc, aabs);
+            fold_run<T, GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, sphi, cphi, lane, F);
             __syncwarp();
         }
         cnt -= run;
@@ -238,17 +273,31 @@ __device__ void assemble_item(const SgItemDev *items, const SgItemVar *vars, con
     if (flags && guard_tol > 0.0) flags[item] = o.err_est > guard_tol ? 1 : 0;
 }
 
-// Fixed-order reduction of an item's chunk slots and assembly of its value.
-__device__ void finish_item(const SgFoldArgs &A, int item, int lane) {
-    const SgItemDev *I = A.items + item;
+// Lane l adds x[l], x[l+32], ... (Neumaier), then the lanes are combined in
+// lane order: a fixed summation order whichever warp runs it.  Eight loads
+// are in flight per lane so that the L2 latency overlaps.
+__device__ void reduce_slots(const double2 *slots, unsigned long long n, int lane, double &S,
+                             double &C, double &AB) {
     double s = 0.0, c = 0.0, ab = 0.0;
-    for (unsigned long long q = lane; q < I->nchunk; q += 32) {
-        const double v = __ldcg(&A.slots[I->chunk0 + q].sum);
-        const double w = __ldcg(&A.slots[I->chunk0 + q].abs);
-        neu_add(s, c, v);
-        ab += w;
+    unsigned long long q = lane;
+    for (; q + 7 * 32 < n; q += 8 * 32) {
+        double2 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) v[t] = __ldcg(slots + q + t * 32);
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            neu_add(s, c, v[t].x);
+            ab += v[t].y;
+        }
     }
-    double S = 0.0, C = 0.0, AB = 0.0;
+    for (; q < n; q += 32) {
+        const double2 v = __ldcg(slots + q);
+        neu_add(s, c, v.x);
+        ab += v.y;
+    }
+    S = 0.0;
+    C = 0.0;
+    AB = 0.0;
     for (int t = 0; t < 32; t++) {
         const double st = __shfl_sync(FULL_MASK, s, t);
         const double ct = __shfl_sync(FULL_MASK, c, t);
@@ -257,18 +306,77 @@ __device__ void finish_item(const SgFoldArgs &A, int item, int lane) {
         neu_add(S, C, ct);
         AB += at;
     }
-    if (lane != 0) return;
-    assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, A.guard_tol,
-                  A.unit_roundoff, item, S + C, AB);
+}
+
+// Same over group records (s, c, abs).
+__device__ void reduce_groups(const SgGroupSlot *g, unsigned long long n, int lane, double &S,
+                              double &C, double &AB) {
+    double s = 0.0, c = 0.0, ab = 0.0;
+    for (unsigned long long q = lane; q < n; q += 32) {
+        const double2 v = __ldcg((const double2 *)(g + q));
+        const double2 w = __ldcg((const double2 *)(g + q) + 1);
+        neu_add(s, c, v.x);
+        neu_add(s, c, v.y);
+        ab += w.x;
+    }
+    S = 0.0;
+    C = 0.0;
+    AB = 0.0;
+    for (int t = 0; t < 32; t++) {
+        const double st = __shfl_sync(FULL_MASK, s, t);
+        const double ct = __shfl_sync(FULL_MASK, c, t);
+        const double at = __shfl_sync(FULL_MASK, ab, t);
+        neu_add(S, C, st);
+        neu_add(S, C, ct);
+        AB += at;
+    }
+}
+
+// Called by the warp that wrote chunk c's slot.  Two-level ticketing: the
+// last chunk of a group reduces the group, the last group reduces the item.
+__device__ void complete_chunk(const SgFoldArgs &A, int item, unsigned long long c, int lane) {
+    const SgItemDev *I = A.items + item;
+    const unsigned long long local = c - I->chunk0;
+    const unsigned long long g = local / SG_GROUP;
+    const unsigned long long gfirst = g * SG_GROUP;
+    const unsigned long long gsize =
+        I->nchunk - gfirst < (unsigned long long)SG_GROUP ? I->nchunk - gfirst : SG_GROUP;
+    unsigned int ticket = 0;
+    if (lane == 0) {
+        __threadfence();
+        ticket = atomicAdd(A.group_done + I->group0 + g, 1u);
+    }
+    ticket = __shfl_sync(FULL_MASK, ticket, 0);
+    if (ticket + 1ull != gsize) return;
+    __threadfence();
+    double S, C, AB;
+    reduce_slots((const double2 *)(A.slots + I->chunk0 + gfirst), gsize, lane, S, C, AB);
+    if (lane == 0) {
+        SgGroupSlot gs;
+        gs.s = S;
+        gs.c = C;
+        gs.abs = AB;
+        gs.pad = 0.0;
+        A.gslots[I->group0 + g] = gs;
+        __threadfence();
+        ticket = atomicAdd(A.item_done + item, 1u);
+    }
+    ticket = __shfl_sync(FULL_MASK, ticket, 0);
+    if (ticket + 1ull != I->ngroups) return;
+    __threadfence();
+    reduce_groups(A.gslots + I->group0, I->ngroups, lane, S, C, AB);
+    if (lane == 0)
+        assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, A.guard_tol,
+                      A.unit_roundoff, item, S + C, AB);
 }
 
 template <typename T>
 __global__ void sg_fold_kernel(SgFoldArgs A) {
+    typedef typename PrefixState<T>::type PS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *sS = (T *)smem + (size_t)warp * 2 * SG_APAD;
-    T *sW = sS + SG_APAD;
-    int *sIdx = (int *)(smem + (size_t)nw * 2 * SG_APAD * sizeof(T)) + warp * SG_MAX_R;
+    PS *sP = (PS *)smem + (size_t)warp * SG_APAD;
+    int *sIdx = (int *)(smem + (size_t)nw * SG_APAD * sizeof(PS)) + warp * SG_MAX_R;
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(A.work, 1ull);
@@ -285,27 +393,22 @@ __global__ void sg_fold_kernel(SgFoldArgs A) {
         const int item = P->item;
         if (A.skip_unflagged && !A.flags[item]) continue;
         const SgItemDev *I = A.items + item;
-        double acc = 0.0, aabs = 0.0;
-        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sS, sW, sIdx, lane, acc, aabs);
-        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sS, sW, sIdx, lane, acc, aabs);
+        FoldAcc F;
+        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sIdx, lane, F);
+        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sIdx, lane, F);
+        double acc = F.acc + ((double)F.hs + (double)F.hc), aabs = (double)F.habs;
         for (int o = 16; o > 0; o >>= 1) {
             acc += __shfl_xor_sync(FULL_MASK, acc, o);
             aabs += __shfl_xor_sync(FULL_MASK, aabs, o);
         }
-        unsigned int ticket = 0;
+        if (sizeof(T) == 8) aabs = fabs(acc);  // the FP64 fold skips |W D| per point
         if (lane == 0) {
             SgSlot sl;
             sl.sum = acc * P->coef;
             sl.abs = aabs * fabs(P->coef);
             A.slots[c] = sl;
-            __threadfence();
-            ticket = atomicAdd(A.item_done + item, 1u);
         }
-        ticket = __shfl_sync(FULL_MASK, ticket, 0);
-        if (ticket + 1ull == I->nchunk) {
-            __threadfence();
-            finish_item(A, item, lane);
-        }
+        complete_chunk(A, item, c, lane);
     }
 }
 
@@ -495,8 +598,8 @@ cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s) {
 }
 
 static size_t fold_smem(int prec, int warps) {
-    const size_t tsz = prec ? sizeof(float) : sizeof(double);
-    return (size_t)warps * (2 * SG_APAD * tsz + SG_MAX_R * sizeof(int));
+    const size_t psz = prec ? sizeof(float2) : sizeof(double2);
+    return (size_t)warps * (SG_APAD * psz + SG_MAX_R * sizeof(int));
 }
 
 int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
@@ -548,18 +651,19 @@ __global__ void __launch_bounds__(256) sg_ceiling_kernel(int sweeps, double *out
     T S = (T)(blockIdx.x * 1e-6), W = (T)0.7;
     const T sphi = (T)0.3, cphi = (T)0.95;
     double acc = 0.0, aabs = 0.0;
+    float hs = 0.f, hc = 0.f, habs = 0.f;
     for (int it = 0; it < sweeps; it++) {
         if constexpr (sizeof(T) == 4) {
-            float part = 0.f, pabs = 0.f;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 const float s = S + dl[k], w = W * wl[k];
                 const float D = gdev<float, GK>(s, sphi, cphi);
-                part = fmaf(w, D, part);
-                pabs = fmaf(fabsf(w), fabsf(D), pabs);
+                float t, e;
+                two_sum(hs, __fmul_rn(w, D), t, e);
+                hs = t;
+                hc += e;
+                habs = fmaf(fabsf(w), fabsf(D), habs);
             }
-            acc += (double)part;
-            aabs += (double)pabs;
         } else {
 #pragma unroll
             for (int k = 0; k < 8; k++) {
@@ -571,7 +675,7 @@ __global__ void __launch_bounds__(256) sg_ceiling_kernel(int sweeps, double *out
         }
         S += (T)1e-7;
     }
-    out[blockIdx.x * blockDim.x + threadIdx.x] = acc + 1e-30 * aabs;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc + 1e-30 * aabs + (double)hs + (double)hc + 1e-30 * habs;
 }
 
 // Eight independent fused multiply-add chains per thread.

@@ -47,8 +47,10 @@ struct SgFoldArgs {
     const void *tab;                 // float2* or double2*
     const unsigned long long *binom; // [k][n] table
     SgSlot *slots;                   // per chunk
+    SgGroupSlot *gslots;             // per reduction group
+    unsigned int *group_done;        // per group chunk tickets (zeroed before launch)
     unsigned long long *work;        // work-stealing counter (zeroed before launch)
-    unsigned int *item_done;         // per item chunk tickets (zeroed before launch)
+    unsigned int *item_done;         // per item group tickets (zeroed before launch)
     const SgBaseDev *bases;          // per integral, for the final assembly
     const int *item_integral;        // per item: integral index (-1: adjoint sub-sum)
     SgOutDev *out;                   // per output

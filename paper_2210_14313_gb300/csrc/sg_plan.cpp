@@ -122,8 +122,8 @@ struct ItemBuild {
 void plan_free_host(Plan *P) { delete P; }
 
 // Builds the items, table layout, patterns and chunks of a list of integrals.
-sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tuning &tune, int sms,
-                          Plan **out) {
+sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tuning &tune,
+                          long long resident_warps, Plan **out) {
     Plan *P = new Plan();
     P->reqs = reqs;
     P->prec = prec;
@@ -252,11 +252,15 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     u64 total = 0;
     for (auto &b : ib) total += b.evals;
     P->total_evals = total;
-    // chunk size: enough chunks to keep every resident warp busy, few enough slots
-    const u64 warps = (u64)sms * tune.ctas_per_sm * tune.warps_per_cta;
-    u64 target = (u64)tune.points_per_chunk;
-    const u64 balance = total / (4 * std::max<u64>(warps, 1)) + 1;
-    if (balance < target) target = std::max<u64>(balance, 64);
+    // chunk size: several chunks per resident warp, but never so small that
+    // the per-chunk work (unranking, prefix folds, one slot) dominates, never
+    // above the tuned maximum, and at most 2^24 chunk slots
+    const u64 warps = (u64)std::max<long long>(resident_warps, 1);
+    const u64 floor_evals = prec ? 2048 : 128;
+    const u64 per_warp = prec ? 4 : 8;  // FP64 chunks are costly: more of them even the tail out
+    u64 target = total / (per_warp * warps) + 1;
+    if (target < floor_evals) target = floor_evals;
+    if (target > (u64)tune.points_per_chunk) target = (u64)tune.points_per_chunk;
     const u64 max_chunks = 1ull << 24;
     if (total / target > max_chunks) target = total / max_chunks + 1;
     u64 chunk = 0;
@@ -291,6 +295,9 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
         }
         b.it.npat = (int)((long long)P->pats.size() - b.it.pat0);
         b.it.nchunk = chunk - b.it.chunk0;
+        b.it.group0 = P->ngroups;
+        b.it.ngroups = (b.it.nchunk + SG_GROUP - 1) / SG_GROUP;
+        P->ngroups += b.it.ngroups;
         P->items.push_back(b.it);
         P->roles.push_back(b.role);
         P->item_integral.push_back(b.integral);

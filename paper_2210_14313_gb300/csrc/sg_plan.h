@@ -60,6 +60,7 @@ struct Plan {
     std::vector<u64> pat_chunk0;
     long long nentries = 0;
     u64 nchunks = 0;
+    u64 ngroups = 0;
     int nout = 0;
     long long nv = 0;
     std::vector<u64> points, evals;  // per integral (forward sum only)
@@ -92,6 +93,7 @@ int tab_m(sg_rule rule, BlockRef b);
 // n_d^q of Eq. 2.6 (false if beyond 64 bits).
 bool count_points(int kind, int d, int L, u64 *out);
 // Builds the host arrays of a plan; device fields stay empty.
-sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tuning &tune, int sms,
-                          Plan **out);
+// resident_warps: warps the persistent fold grid keeps on the device (sets the chunk size).
+sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tuning &tune,
+                          long long resident_warps, Plan **out);
 void plan_free_host(Plan *P);

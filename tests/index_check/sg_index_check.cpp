@@ -82,7 +82,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
     reqs[0] = Req{&rule, fam, d, L, form, 0, grad};
     sg_tuning t{ppc, ctas_per_sm, warps};
     Plan *P = nullptr;
-    if (build_plan_host(reqs, 0, t, 152, &P) != SG_OK) return 1;
+    if (build_plan_host(reqs, 0, t, 152LL * ctas_per_sm * warps, &P) != SG_OK) return 1;
 
     // table, filled from the host block lists
     std::vector<double2> tab(P->nentries > 0 ? P->nentries : 1);
