@@ -259,6 +259,29 @@ SG_API sg_status sg_profile_end(void *stream, double *fold_ms, int *launches);
  */
 SG_API sg_status sg_ceiling(sg_precision prec, int kind, void *stream, double *rate);
 
+/*
+ * One integral without any memory allocation (the paper has no counterpart;
+ * this exists for callers that must not allocate).  Some callers cannot call
+ * cudaMalloc or any allocator where they integrate: a host thread in a
+ * latency-critical loop (cudaMalloc/cudaFree synchronise the device and
+ * stall other streams), or a runtime that owns all device memory and forbids
+ * libraries to allocate behind its back.  This entry point takes the rule
+ * kind instead of a handle, device params (2d doubles) and a device result
+ * record, like sg_integrate_async, and uses the telescoped form.  Its device
+ * scratch is one fixed array of about 4.2 MB inside the library, held by
+ * every GPU that loads the library until the process exits.
+ * Limits: 1 <= d <= 1024, 0 <= q - d <= 6, at most 131072 table entries
+ * (d times the summed node counts of the rule blocks) and 65536 work chunks;
+ * larger problems return SG_ERANGE.  The first call on a device (with that
+ * device current) resolves the array's address and uploads a table with a
+ * synchronous copy: make it before any stream capture.  All calls share the
+ * array and leave their data in it (work tickets are cleared at the start of
+ * each call); calls that overlap on the GPU race on it and must be
+ * serialised by the caller.  Errors: SG_EINVAL, SG_ERANGE, SG_ECUDA.
+ */
+SG_API sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, const double *d_params, int d,
+                                      int q, sg_precision prec, void *stream, sg_dev_result *d_out);
+
 #ifdef __cplusplus
 }
 #endif
