@@ -260,6 +260,16 @@ SG_API sg_status sg_profile_end(void *stream, double *fold_ms, int *launches);
 SG_API sg_status sg_ceiling(sg_precision prec, int kind, void *stream, double *rate);
 
 /*
+ * Accuracy hook (no counterpart in the paper): evaluates the elementary
+ * functions the fold uses per point, in the given precision, on n device
+ * arguments d_x.  kind 0: y[i] = expm1(x[i]); kind 1: y[2i] = sin(x[i]),
+ * y[2i+1] = cos(x[i]).  d_y is caller-owned device memory (n or 2n
+ * doubles).  Asynchronous on `stream`.  Errors: SG_EINVAL, SG_ECUDA.
+ */
+SG_API sg_status sg_eval_functions(int kind, sg_precision prec, const double *d_x, double *d_y, int n,
+                                   void *stream);
+
+/*
  * One integral without any memory allocation (the paper has no counterpart;
  * this exists for callers that must not allocate).  Some callers cannot call
  * cudaMalloc or any allocator where they integrate: a host thread in a

@@ -32,7 +32,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ERANGE", 3: "SG_ENOMEM", 4: "
 ABI_SYMBOLS = ["sg_rule_init", "sg_rule_destroy", "sg_rule_nodes", "sg_count_points",
                "sg_integrate", "sg_integrate_async", "sg_integrate_batch", "sg_integrate_grad",
                "sg_status_string", "sg_get_tuning", "sg_set_tuning", "sg_autotune",
-               "sg_profile_begin", "sg_profile_end", "sg_ceiling", "sg_integrate_noalloc"]
+               "sg_profile_begin", "sg_profile_end", "sg_ceiling", "sg_integrate_noalloc",
+               "sg_eval_functions"]
 
 
 class SgError(RuntimeError):
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = True):
     lib.sg_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.sg_ceiling.argtypes = [ip, ip, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sg_integrate_noalloc.argtypes = [ip, ip, vp, ip, ip, ip, vp, vp]
+    lib.sg_eval_functions.argtypes = [ip, ip, vp, vp, ip, vp]
     for name in ABI_SYMBOLS:
         if name != "sg_status_string":
             getattr(lib, name).restype = ctypes.c_int

@@ -930,3 +930,12 @@ extern "C" sg_status sg_ceiling(sg_precision prec, int kind, void *stream, doubl
     *rate = work / (best * 1e-3);
     return SG_OK;
 }
+
+extern "C" sg_status sg_eval_functions(int kind, sg_precision prec, const double *d_x, double *d_y, int n,
+                                       void *stream) {
+    if (!d_x || !d_y || n < 0 || kind < 0 || kind > 1) return SG_EINVAL;
+    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    cudaGetLastError();
+    CK(sg_launch_fn(kind, prec, d_x, d_y, n, (cudaStream_t)stream));
+    return SG_OK;
+}

@@ -85,10 +85,31 @@ template <typename T> struct V2T;
 template <> struct V2T<float> { typedef float2 type; };
 template <> struct V2T<double> { typedef double2 type; };
 
+// expm1 in float for the fold's argument range (no special-case paths): Cody & Waite argument reduction x = k ln2 + r, |r| <= ln2/2,
+// with ln 2 split so that k * ln2_hi is exact, the Taylor series of
+// expm1(r) to degree 8 (truncation below 2.1e-10 relative), and
+// expm1(x) = 2^k expm1(r) + (2^k - 1), which is r's series itself when
+// k = 0.  k is clamped to [-126, 127]: below -87 the result is -1 to float
+// precision; the fold's arguments stay far below the overflow end.
+__device__ __forceinline__ float sg_expm1f(float x) {
+    const float k = fminf(fmaxf(rintf(x * 1.44269504088896341f), -126.f), 127.f);
+    float r = fmaf(-k, 6.93145752e-1f, x);
+    r = fmaf(-k, 1.42860677e-6f, r);
+    float h = fmaf(r, 2.48015873e-5f, 1.98412698e-4f);  // 1/8!, 1/7!
+    h = fmaf(h, r, 1.38888889e-3f);                     // 1/6!
+    h = fmaf(h, r, 8.33333333e-3f);                     // 1/5!
+    h = fmaf(h, r, 4.16666667e-2f);                     // 1/4!
+    h = fmaf(h, r, 1.66666667e-1f);                     // 1/3!
+    h = fmaf(h, r, 0.5f);
+    const float p = fmaf(r * r, h, r);
+    const float scale = __int_as_float(((int)k + 127) << 23);
+    return fmaf(scale, p, scale - 1.0f);
+}
+
 // Per-point deviation (the "G" evaluation).
 template <typename T, int GK> __device__ __forceinline__ T gdev(T S, T sphi, T cphi);
 template <> __device__ __forceinline__ float gdev<float, SG_GK_EXPM1>(float S, float, float) {
-    return expm1f(S);
+    return sg_expm1f(S);
 }
 template <> __device__ __forceinline__ double gdev<double, SG_GK_EXPM1>(double S, double, double) {
     return expm1(S);
@@ -715,4 +736,34 @@ double sg_launch_ceiling(int prec, int kind, int sms, double *d_out, cudaStream_
         }
     }
     return per * sweeps;
+}
+
+// ---------------------------------------------------------------------------
+// function check: the fold's elementary functions on given arguments
+// ---------------------------------------------------------------------------
+
+__global__ void sg_fn_kernel(int kind, int prec, const double *x, double *y, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (kind == 0) {
+        y[i] = prec ? (double)sg_expm1f((float)x[i]) : expm1(x[i]);
+    } else {
+        if (prec) {
+            float s, c;
+            sincosf((float)x[i], &s, &c);
+            y[2 * i] = s;
+            y[2 * i + 1] = c;
+        } else {
+            double s, c;
+            sincos(x[i], &s, &c);
+            y[2 * i] = s;
+            y[2 * i + 1] = c;
+        }
+    }
+}
+
+cudaError_t sg_launch_fn(int kind, int prec, const double *x, double *y, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    sg_fn_kernel<<<(n + 255) / 256, 256, 0, s>>>(kind, prec, x, y, n);
+    return cudaGetLastError();
 }

@@ -114,3 +114,8 @@ cudaError_t sg_launch_grad(const SgGradArgs &a, cudaStream_t s);
 // Ceiling microbenchmarks (see sg_ceiling in include/sg.h).  Returns the
 // number of points (or flops) one launch performs.
 double sg_launch_ceiling(int prec, int kind, int sms, double *d_out, cudaStream_t s);
+
+// Evaluates the fold's elementary functions (kind 0: expm1 -> y[i]; kind 1:
+// sincos -> y[2i], y[2i+1]) in precision prec (0 double, 1 float) on device
+// arrays, for accuracy tests.
+cudaError_t sg_launch_fn(int kind, int prec, const double *x, double *y, int n, cudaStream_t s);
