@@ -159,7 +159,7 @@ extern "C" sg_status sg_rule_nodes(sg_rule r, int level, double *x, double *w, i
 // ---------------------------------------------------------------------------
 
 // index 0: FP64, 1: mixed
-static sg_tuning g_tune[2] = {{2048, 8, 8}, {16384, 8, 8}};
+static sg_tuning g_tune[2] = {{2048, 4, 4}, {32768, 8, 4}};
 
 extern "C" sg_status sg_get_tuning(sg_precision prec, sg_tuning *t) {
     if (!t || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED)) return SG_EINVAL;

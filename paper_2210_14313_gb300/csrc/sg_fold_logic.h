@@ -90,3 +90,23 @@ SG_HD long long sg_prefix_entry(const SgPatDev *P, int t, int dir_actual, int *q
     *q /= m;
     return P->poff[t] + (long long)dir_actual * m + jt;
 }
+
+// Work of chunk c of pattern P: subsets [rank, rank + cnt) and prefix node
+// tuples [a_lo, a_hi).  A subset with more points than the chunk target is
+// split over several chunks by prefix-tuple blocks (then cnt = 1).
+SG_HD void sg_chunk_span(const SgPatDev *P, unsigned long long c, unsigned long long *rank,
+                         unsigned long long *cnt, int *a_lo, int *a_hi) {
+    const unsigned long long local = c - P->chunk0;
+    if (P->asplit <= 1) {
+        *rank = local * P->spc;
+        *cnt = P->nsub - *rank < P->spc ? P->nsub - *rank : P->spc;
+        *a_lo = 0;
+        *a_hi = P->A;
+    } else {
+        *rank = local / (unsigned long long)P->asplit;
+        *cnt = 1;
+        const int blk = (int)(local - *rank * (unsigned long long)P->asplit);
+        *a_lo = blk * P->ablk;
+        *a_hi = *a_lo + P->ablk < P->A ? *a_lo + P->ablk : P->A;
+    }
+}

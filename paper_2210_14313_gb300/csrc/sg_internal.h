@@ -78,7 +78,9 @@ struct SgPatDev {
     int pm[SG_MAX_R - 1];          // nodes per direction of the prefix blocks
     double coef;      // multiplier of the pattern's sum (1, or Eq. 2.6 coefficient)
     unsigned long long nsub;   // C(d, r) subsets
-    unsigned long long spc;    // subsets per chunk
+    unsigned long long spc;    // subsets per chunk (1 when a subset is split)
+    int asplit;                // chunks per subset (prefix-tuple blocks); 1 = no split
+    int ablk;                  // prefix tuples per block when split
     unsigned long long chunk0; // first global chunk of this pattern
 };
 

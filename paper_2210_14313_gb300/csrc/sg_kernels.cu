@@ -64,6 +64,14 @@ __device__ __forceinline__ double phi_dev(int fam, double a, double u, double x)
     return 0.0;
 }
 
+// Table value of a direction's deviation: phi_dev, except that the
+// oscillatory family stores half the phase deviation, so that the per-point
+// deviation -2 sin(S/2) sin(phi + S/2) needs no halving of the folded S.
+__device__ __forceinline__ double phi_table(int fam, double a, double u, double x) {
+    const double v = phi_dev(fam, a, u, x);
+    return fam == 1 ? 0.5 * v : v;
+}
+
 // phi_i(1/2): the direction's share of log f(c) (exponential families) or of
 // the phase (oscillatory).
 __device__ __forceinline__ double phi_centre(int fam, double a, double u) {
@@ -114,16 +122,22 @@ template <> __device__ __forceinline__ float gdev<float, SG_GK_EXPM1>(float S, f
 template <> __device__ __forceinline__ double gdev<double, SG_GK_EXPM1>(double S, double, double) {
     return expm1(S);
 }
-template <> __device__ __forceinline__ float gdev<float, SG_GK_OSC>(float S, float sphi, float cphi) {
+// Oscillatory: H is half the folded phase deviation; returns
+// sin(H) sin(phi + H), and the factor -2 of
+// cos(phi + 2H) - cos(phi) = -2 sin(H) sin(phi + H) sits in the weights.
+template <> __device__ __forceinline__ float gdev<float, SG_GK_OSC>(float H, float sphi, float cphi) {
     float sh, ch;
-    sincosf(0.5f * S, &sh, &ch);
-    return -2.0f * sh * fmaf(sphi, ch, cphi * sh);
+    sincosf(H, &sh, &ch);
+    return sh * fmaf(sphi, ch, cphi * sh);
 }
-template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double S, double sphi, double cphi) {
+template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double H, double sphi, double cphi) {
     double sh, ch;
-    sincos(0.5 * S, &sh, &ch);
-    return -2.0 * sh * fma(sphi, ch, cphi * sh);
+    sincos(H, &sh, &ch);
+    return sh * fma(sphi, ch, cphi * sh);
 }
+
+// Weight factor of the deviation kind (see gdev).
+template <int GK> __device__ __forceinline__ double gdev_weight() { return GK == SG_GK_OSC ? -2.0 : 1.0; }
 
 // ---------------------------------------------------------------------------
 // the fold: one chunk of one pattern, processed by one warp
@@ -223,23 +237,24 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                            typename PrefixState<T>::type *sP, int *sIdx, int lane, FoldAcc &F) {
     typedef typename V2T<T>::type V2;
     const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
-    const int d = I->d, r = P->r, skip = I->skip, Atot = P->A, tm = P->tm;
+    const int d = I->d, r = P->r, skip = I->skip, tm = P->tm;
     const SgItemVar *V = A.vars + (I - A.items);
     const T sphi = (T)V->sin_phi, cphi = (T)V->cos_phi;
-    const unsigned long long rank = (c - P->chunk0) * P->spc;
-    unsigned long long cnt = P->nsub - rank < P->spc ? P->nsub - rank : P->spc;
+    unsigned long long rank, cnt;
+    int a_lo, a_hi;
+    sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
     if (lane == 0) sg_unrank_lex(rank, d, r, A.binom, sIdx);
     __syncwarp();
     while (cnt > 0) {
         const int plast = sIdx[r - 1];
         const int run = (unsigned long long)(d - plast) < cnt ? d - plast : (int)cnt;
         const SgTailSegs seg = sg_tail_segments(P->toff, tm, plast, run, skip);
-        for (int ab = 0; ab < Atot; ab += SG_APAD) {
-            const int At = Atot - ab < SG_APAD ? Atot - ab : SG_APAD;
+        for (int ab = a_lo; ab < a_hi; ab += SG_APAD) {
+            const int At = a_hi - ab < SG_APAD ? a_hi - ab : SG_APAD;
             // fold the prefix directions: one state per prefix node tuple
             for (int a = lane; a < At; a += 32) {
                 int q = ab + a;
-                T S = 0, W = 1;
+                T S = 0, W = (T)gdev_weight<GK>();
                 for (int t = r - 2; t >= 0; t--) {
                     const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
                     S += e.x;
@@ -392,7 +407,7 @@ __device__ void complete_chunk(const SgFoldArgs &A, int item, unsigned long long
 }
 
 template <typename T>
-__global__ void sg_fold_kernel(SgFoldArgs A) {
+__device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     typedef typename PrefixState<T>::type PS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -432,6 +447,11 @@ __global__ void sg_fold_kernel(SgFoldArgs A) {
         complete_chunk(A, item, c, lane);
     }
 }
+
+// Float fold: register budget for 4 CTAs of 8 warps per SM.  Double fold:
+// no occupancy constraint (a few warps already saturate GB300's FP64 pipe).
+__global__ void __launch_bounds__(256, 4) sg_fold_kernel_f(SgFoldArgs A) { fold_kernel_body<float>(A); }
+__global__ void sg_fold_kernel_d(SgFoldArgs A) { fold_kernel_body<double>(A); }
 
 // ---------------------------------------------------------------------------
 // setup: per-integral base quantities and the (phi, w) tables
@@ -490,7 +510,7 @@ __global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
         const int i = (int)(local / B.m), j = (int)(local - (long long)i * B.m);
         const double2 xw = B.xw[j];
         const double *p = A.params + G.param_off;
-        const double phi = phi_dev(G.fam, p[i], p[G.d + i], xw.x);
+        const double phi = phi_table(G.fam, p[i], p[G.d + i], xw.x);
         if (A.tab64) A.tab64[B.off + local] = make_double2(phi, xw.y);
         if (A.tab32) A.tab32[B.off + local] = make_float2((float)phi, (float)xw.y);
     }
@@ -628,17 +648,17 @@ int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
     int n = 0;
     const size_t sm = fold_smem(prec, warps_per_cta);
     if (prec)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel<float>, 32 * warps_per_cta, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_f, 32 * warps_per_cta, sm);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel<double>, 32 * warps_per_cta, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_d, 32 * warps_per_cta, sm);
     return n;
 }
 
 cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cfg, cudaStream_t s) {
     (void)gk;
     const size_t sm = fold_smem(prec, cfg.warps_per_cta);
-    if (prec) sg_fold_kernel<float><<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
-    else sg_fold_kernel<double><<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
+    if (prec) sg_fold_kernel_f<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
+    else sg_fold_kernel_d<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
     return cudaGetLastError();
 }
 

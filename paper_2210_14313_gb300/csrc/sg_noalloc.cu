@@ -274,9 +274,20 @@ sg_status na_plan(int kind, int fam, int d, int L, int prec, long long resident_
         pd.toff = P.blk_off[spec[i].tail];
         pd.coef = 1.0;
         pd.nsub = nsub;
-        pd.spc = target / per[i] > 0 ? target / per[i] : 1;
         pd.chunk0 = chunk;
-        chunk += (nsub + pd.spc - 1) / pd.spc;
+        if (per[i] > target && A > 1) {
+            unsigned long long parts = (per[i] + target - 1) / target;
+            if (parts > A) parts = A;
+            pd.ablk = (int)((A + parts - 1) / parts);
+            pd.asplit = (int)((A + pd.ablk - 1) / pd.ablk);
+            pd.spc = 1;
+            chunk += nsub * (unsigned long long)pd.asplit;
+        } else {
+            pd.asplit = 1;
+            pd.ablk = (int)A;
+            pd.spc = target / per[i] > 0 ? target / per[i] : 1;
+            chunk += (nsub + pd.spc - 1) / pd.spc;
+        }
         P.pat_chunk0[P.npat] = pd.chunk0;
         P.npat++;
     }

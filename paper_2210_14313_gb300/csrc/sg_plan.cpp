@@ -256,7 +256,7 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     // the per-chunk work (unranking, prefix folds, one slot) dominates, never
     // above the tuned maximum, and at most 2^24 chunk slots
     const u64 warps = (u64)std::max<long long>(resident_warps, 1);
-    const u64 floor_evals = prec ? 2048 : 128;
+    const u64 floor_evals = prec ? 2048 : 32;
     const u64 per_warp = prec ? 4 : 8;  // FP64 chunks are costly: more of them even the tail out
     u64 target = total / (per_warp * warps) + 1;
     if (target < floor_evals) target = floor_evals;
@@ -287,9 +287,22 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
             pd.tm = tab_m(rule, sp.tail);
             pd.toff = relmap[g].at(sp.tail);
             pd.coef = sp.coef;
-            pd.spc = std::max<u64>(1, target / (A * (u64)pd.tm));
+            const u64 per_sub = A * (u64)pd.tm;
             pd.chunk0 = chunk;
-            chunk += (pd.nsub + pd.spc - 1) / pd.spc;
+            if (per_sub > target && A > 1) {
+                // split each subset's prefix tuples over several chunks
+                u64 parts = (per_sub + target - 1) / target;
+                if (parts > A) parts = A;
+                pd.ablk = (int)((A + parts - 1) / parts);
+                pd.asplit = (int)((A + pd.ablk - 1) / pd.ablk);
+                pd.spc = 1;
+                chunk += pd.nsub * (u64)pd.asplit;
+            } else {
+                pd.asplit = 1;
+                pd.ablk = (int)A;
+                pd.spc = std::max<u64>(1, target / per_sub);
+                chunk += (pd.nsub + pd.spc - 1) / pd.spc;
+            }
             P->pats.push_back(pd);
             P->pat_chunk0.push_back(pd.chunk0);
         }

@@ -155,8 +155,10 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
         const SgItemVar &V = var[Pp->item];
         const long long tbase = I->tab;
         const int dd = I->d, r = Pp->r, skip = I->skip;
-        const unsigned long long rank = (c - Pp->chunk0) * Pp->spc;
-        unsigned long long cnt = Pp->nsub - rank < Pp->spc ? Pp->nsub - rank : Pp->spc;
+        unsigned long long rank, cnt;
+        int a_lo, a_hi;
+        sg_chunk_span(Pp, c, &rank, &cnt, &a_lo, &a_hi);
+        if (a_lo < 0 || a_hi > Pp->A || a_lo >= a_hi) violations++;
         sg_unrank_lex(rank, dd, r, B.data(), idx);
         for (int t = 1; t < r; t++)
             if (idx[t] <= idx[t - 1]) violations++;
@@ -180,7 +182,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
             const int E = seg.E1 + seg.E2;
             if (E != run * Pp->tm) violations++;
             std::vector<double> S(Pp->A), W(Pp->A);
-            for (int a = 0; a < Pp->A; a++) {
+            for (int a = a_lo; a < a_hi; a++) {
                 int q = a;
                 double s = 0, w = 1;
                 for (int tt = r - 2; tt >= 0; tt--) {
@@ -196,8 +198,8 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
                 W[a] = w;
             }
             // replay the lane split of fold_run (one pass per prefix tile)
-            for (int ab = 0; ab < Pp->A; ab += SG_APAD) {
-                const int At = Pp->A - ab < SG_APAD ? Pp->A - ab : SG_APAD;
+            for (int ab = a_lo; ab < a_hi; ab += SG_APAD) {
+                const int At = a_hi - ab < SG_APAD ? a_hi - ab : SG_APAD;
                 std::vector<int> seen((size_t)At * E, 0);
                 const int G = E >= 32 ? 1 : 32 / E, Eg = E >= 32 ? 32 : E;
                 for (int lane = 0; lane < 32; lane++) {
