@@ -252,6 +252,8 @@ def run_gpu(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
+    if rank == 0 and ws == 1 and not args.no_extra:
+        line["extra"] = _extras(sg, oracle, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         oracle.build()
         rate, n, dt = _oracle_rate(c)
@@ -261,6 +263,57 @@ def run_gpu(args):
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def _extras(sg, oracle, torch):
+    """Precision ladder on every configuration and a batch subset (one GPU):
+    seconds per integral and relative error against the oracle."""
+    import numpy as np
+    import sg_inputs as si
+    rules = {k: sg.Rule(k, max_level=8) for k in (2, 4)}
+    out = {"configs": {}, "batch": {}}
+    names = {0: "fp64", 1: "mixed", 2: "ff"}
+    for c in [si.cfg1(), si.cfg2(), si.cfg3(si.FAM_PRODUCT_PEAK), si.cfg3(si.FAM_GAUSSIAN), si.cfg5()]:
+        ref = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
+        row = {"points": oracle.count_points(c["rule"], c["d"], c["L"])}
+        for prec in (0, 1, 2):
+            ts = []
+            for _ in range(7):
+                r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec)
+                ts.append(r.seconds)
+            t = sorted(ts)[3]
+            err = abs(r.mant * 2.0 ** (r.exp2 - ref.exp2) - ref.mant) / abs(ref.mant)
+            row[names[prec]] = {"s_per_integral": t, "points_per_s": row["points"] / t, "rel_err": err,
+                                "err_est": r.err_est}
+        out["configs"][c["name"]] = row
+    # batch subset: the first items of the 4096-item workload whose point
+    # count stays below 5e9 (so that the FP64 form finishes in seconds)
+    items = [it for it in si.batch()[:1200]
+             if oracle.count_points(it["rule"], it["d"], it["L"]) <= 5e9][:96]
+    specs, pool, off = [], [], 0
+    for it in items:
+        specs.append((rules[it["rule"]], it["fam"], it["d"], it["d"] + it["L"], off))
+        pool.append(np.asarray(it["params"]))
+        off += 2 * it["d"]
+    pool = np.concatenate(pool)
+    pts = sum(oracle.count_points(it["rule"], it["d"], it["L"]) for it in items)
+    small = [k for k, it in enumerate(items)
+             if oracle.count_points(it["rule"], it["d"], it["L"]) <= 5e6][:24]
+    refs = [oracle.integrate(items[k]["rule"], items[k]["fam"], items[k]["params"], items[k]["d"],
+                             items[k]["L"]) for k in small]
+    out["batch"]["items"] = len(items)
+    out["batch"]["points"] = pts
+    for label, prec, g in (("fp64", 0, 0.0), ("mixed", 1, 0.0), ("mixed_guard_ff_1e-6", 1, 2.5e-7), ("ff", 2, 0.0)):
+        sg.integrate_batch(specs, pool, prec=prec, guard_tol=g)
+        res = sg.integrate_batch(specs, pool, prec=prec, guard_tol=g)
+        t = res[0].seconds
+        errs = [abs(res[k].mant * 2.0 ** (res[k].exp2 - o.exp2) - o.mant) / abs(o.mant)
+                for k, o in zip(small, refs)]
+        out["batch"][label] = {"s": t, "points_per_s": pts / t,
+                               "max_rel_err_vs_oracle": max(errs) if errs else None,
+                               "oracle_checked_items": len(errs),
+                               "max_err_est": max(r.err_est for r in res)}
+    return out
 
 
 def sg_family_name(f):
@@ -276,6 +329,7 @@ def main():
     ap.add_argument("--workload", default="cfg2")
     ap.add_argument("--prec", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -81,9 +81,12 @@ typedef enum {
 
 typedef enum {
     SG_PREC_FP64 = 0,   /* every step in IEEE double */
-    SG_PREC_MIXED = 1   /* integrand evaluation and per-cluster folds in float;
+    SG_PREC_MIXED = 1,  /* integrand evaluation and per-cluster folds in float;
                            cross-cluster and cross-chunk sums in double with
                            Neumaier compensation */
+    SG_PREC_FF = 2      /* float-float: tables, folds and the per-point deviation
+                           as unevaluated pairs of floats (about 44 bits) on the
+                           FP32 pipes; cross-chunk sums in double */
 } sg_precision;
 
 /* Which algebraic form of the same Smolyak sum the kernels enumerate.  All
@@ -187,8 +190,8 @@ typedef struct {
  * cached for this batch layout.  params_pool: host (params_on_device = 0) or
  * device memory; item k reads pool[param_offset .. param_offset + 2d).
  * With prec = SG_PREC_MIXED and guard_tol > 0, items whose estimated
- * rounding error exceeds guard_tol are recomputed in FP64 by a second
- * persistent launch in the same graph.  out: n host records.  Blocking.
+ * rounding error exceeds guard_tol are recomputed in float-float
+ * (SG_PREC_FF) by a second persistent launch in the same graph.  out: n host records.  Blocking.
  * Limits: 1 <= n <= 65536, per item as sg_integrate.
  */
 SG_API sg_status sg_integrate_batch(const sg_item *items, int n, const double *params_pool,

@@ -21,7 +21,7 @@ from ._build import LIB as _LIB_PATH, build as _build_lib
 # enums of include/sg.h
 RULE_TRAPEZOID, RULE_CLENSHAW_CURTIS, RULE_GAUSS_LEGENDRE = 1, 2, 4
 FAM_EXP_LINEAR, FAM_OSCILLATORY, FAM_PRODUCT_PEAK, FAM_GAUSSIAN, FAM_GAUSSIAN_LIN = 0, 1, 2, 3, 4
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FF = 0, 1, 2
 FORM_AUTO, FORM_DIFFERENCE, FORM_TELESCOPED, FORM_COMBINATION = 0, 1, 2, 3
 
 SG_OK = 0

@@ -158,18 +158,20 @@ extern "C" sg_status sg_rule_nodes(sg_rule r, int level, double *x, double *w, i
 // tuning
 // ---------------------------------------------------------------------------
 
-// index 0: FP64, 1: mixed
-static sg_tuning g_tune[2] = {{2048, 4, 4}, {32768, 8, 4}};
+// index 0: FP64, 1: mixed, 2: float-float
+static sg_tuning g_tune[3] = {{2048, 4, 4}, {32768, 8, 4}, {8192, 3, 8}};
+
+static bool prec_ok(int p) { return p == SG_PREC_FP64 || p == SG_PREC_MIXED || p == SG_PREC_FF; }
 
 extern "C" sg_status sg_get_tuning(sg_precision prec, sg_tuning *t) {
-    if (!t || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED)) return SG_EINVAL;
+    if (!t || !prec_ok(prec)) return SG_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
     *t = g_tune[prec];
     return SG_OK;
 }
 
 extern "C" sg_status sg_set_tuning(sg_precision prec, const sg_tuning *t) {
-    if (!t || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED)) return SG_EINVAL;
+    if (!t || !prec_ok(prec)) return SG_EINVAL;
     if (t->points_per_chunk < 32 || t->points_per_chunk > (1 << 26) || t->ctas_per_sm < 1 ||
         t->ctas_per_sm > 32 || t->warps_per_cta < 1 || t->warps_per_cta > 32)
         return SG_ERANGE;
@@ -346,7 +348,7 @@ struct GraphEntry {
 struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
-    DevBuf tab32, tab64, slots, gslots, counters, flags, bases, vars, out, vout, grad, params;
+    DevBuf tab32, tab64, tabff, slots, gslots, counters, flags, bases, vars, out, vout, grad, params;
     void *h_pinned = nullptr;
     size_t h_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_join = nullptr;
@@ -450,14 +452,20 @@ static sg_status ensure_host(Workspace *W, size_t bytes) {
         if (s_ != SG_OK) return s_;      \
     } while (0)
 
+// Unit roundoff of a precision (float-float: about 44 significant bits).
+static double unit_roundoff(int prec) {
+    return prec == 1 ? 5.9604644775390625e-08 : (prec == 2 ? 5.6843418860808015e-14 : 1.1102230246251565e-16);
+}
+
 // Counters: [u64 work][u32 item tickets][u32 group tickets], zeroed per launch.
 static size_t counter_bytes(const Plan *P) { return 16 + 4 * (P->items.size() + P->ngroups); }
 
 // Makes every buffer a plan needs large enough (outside any capture).
-static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need64,
+static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need64, bool needff,
                             size_t param_doubles) {
     if (need32) ST(ensure(W, W->tab32, (size_t)P->nentries * sizeof(float2)));
     if (need64) ST(ensure(W, W->tab64, (size_t)P->nentries * sizeof(double2)));
+    if (needff) ST(ensure(W, W->tabff, (size_t)P->nentries * sizeof(float4)));
     ST(ensure(W, W->slots, (size_t)P->nchunks * sizeof(SgSlot)));
     ST(ensure(W, W->gslots, (size_t)P->ngroups * sizeof(SgGroupSlot)));
     ST(ensure(W, W->counters, counter_bytes(P)));
@@ -501,12 +509,13 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     sa.integrals = P->d_integrals;
     sa.nintegrals = (int)P->integrals.size();
     sa.params = d_params;
-    sa.tab32 = prec ? (float2 *)W->tab32.p : nullptr;
-    sa.tab64 = prec ? nullptr : (double2 *)W->tab64.p;
+    sa.tab32 = prec == 1 ? (float2 *)W->tab32.p : nullptr;
+    sa.tab64 = prec == 0 ? (double2 *)W->tab64.p : nullptr;
+    sa.tabff = prec == 2 ? (float4 *)W->tabff.p : nullptr;
     sa.bases = (SgBaseDev *)W->bases.p;
     sa.flags = nullptr;
     CK(sg_launch_setup(sa, s));
-    const double u = prec ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    const double u = unit_roundoff(prec);
     SgPrepArgs pa;
     pa.roles = P->d_roles;
     pa.items = P->d_items;
@@ -531,7 +540,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     fa.pat_chunk0 = P->d_pat_chunk0;
     fa.npat = (long long)P->pats.size();
     fa.nchunks = P->nchunks;
-    fa.tab = prec ? W->tab32.p : W->tab64.p;
+    fa.tab = prec == 1 ? W->tab32.p : (prec == 2 ? W->tabff.p : W->tab64.p);
     fa.binom = C->binom;
     fa.slots = (SgSlot *)W->slots.p;
     fa.work = (unsigned long long *)W->counters.p;
@@ -550,18 +559,18 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
     CK(prof_mark(W, false, s));
     if (prec == 1 && guard_tol > 0.0) {
-        // precision guard: recompute flagged items in FP64
+        // precision guard: recompute flagged items in float-float
         CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
         sa.tab32 = nullptr;
-        sa.tab64 = (double2 *)W->tab64.p;
+        sa.tabff = (float4 *)W->tabff.p;
         sa.flags = (int *)W->flags.p;
         CK(sg_launch_setup(sa, s));
-        fa.tab = W->tab64.p;
+        fa.tab = W->tabff.p;
         fa.skip_unflagged = (int *)W->flags.p;
         fa.guard_tol = 0.0;
-        fa.unit_roundoff = 1.1102230246251565e-16;
+        fa.unit_roundoff = unit_roundoff(2);
         CK(prof_mark(W, true, s));
-        CK(sg_launch_fold(fa, 0, 0, fold_cfg(P, 0, C), s));
+        CK(sg_launch_fold(fa, 2, 0, fold_cfg(P, 2, C), s));
         CK(prof_mark(W, false, s));
     }
     return SG_OK;
@@ -575,7 +584,7 @@ static sg_status check_one(sg_rule rule, sg_family fam, int d, int q, sg_precisi
                            sg_form *form) {
     if (!rule) return SG_EINVAL;
     if ((int)fam < 0 || (int)fam > 4) return SG_EINVAL;
-    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    if (!prec_ok(prec)) return SG_EINVAL;
     if ((int)*form < 0 || (int)*form > 3) return SG_EINVAL;
     if (*form == SG_FORM_AUTO) *form = SG_FORM_TELESCOPED;
     if (d < 1 || q < d) return SG_EINVAL;
@@ -643,7 +652,7 @@ extern "C" sg_status sg_integrate_async(sg_rule rule, sg_family fam, const doubl
     ST(get_plan(reqs, prec, &P));
     Workspace *W = nullptr;
     ST(get_ws((cudaStream_t)stream, &W));
-    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, 0));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, prec == SG_PREC_FF, 0));
     return run_plan(P, W, C, d_params, 0.0, (SgOutDev *)d_out, (cudaStream_t)stream);
 }
 
@@ -664,7 +673,8 @@ extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *par
     Workspace *W = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     ST(get_ws(s, &W));
-    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, params_on_device ? 0 : 2 * (size_t)d));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, prec == SG_PREC_FF,
+                  params_on_device ? 0 : 2 * (size_t)d));
     ST(ensure_host(W, sizeof(SgOutDev)));
     const double *dp = params;
     if (!params_on_device) {
@@ -703,9 +713,9 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
                                         int params_on_device, sg_precision prec, double guard_tol,
                                         void *stream, sg_result *out) {
     if (!params_pool || !out) return SG_EINVAL;
-    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    if (!prec_ok(prec)) return SG_EINVAL;
     if (!(guard_tol >= 0.0)) return SG_EINVAL;
-    if (prec == SG_PREC_FP64) guard_tol = 0.0;
+    if (prec != SG_PREC_MIXED) guard_tol = 0.0;
     std::vector<Req> reqs;
     size_t pool = 0;
     ST(batch_reqs(items, n, reqs, &pool));
@@ -719,7 +729,8 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     ST(get_ws(s, &W));
     const bool guard = prec == SG_PREC_MIXED && guard_tol > 0.0;
-    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64 || guard, params_on_device ? 0 : pool));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, prec == SG_PREC_FF || guard,
+                  params_on_device ? 0 : pool));
     ST(ensure_host(W, (size_t)P->nout * sizeof(SgOutDev)));
     // graphs run on the workspace's own stream, ordered after the caller's work
     cudaStream_t g = W->own;
@@ -782,7 +793,8 @@ extern "C" sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double
     Workspace *W = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     ST(get_ws(s, &W));
-    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, params_on_device ? 0 : 2 * (size_t)d));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, prec == SG_PREC_FF,
+                  params_on_device ? 0 : 2 * (size_t)d));
     ST(ensure_host(W, sizeof(SgOutDev) + 2 * (size_t)d * sizeof(double)));
     const double *dp = params;
     if (!params_on_device) {
@@ -839,7 +851,7 @@ extern "C" sg_status sg_autotune(const sg_item *items, int n, const double *para
                                  int params_on_device, sg_precision prec, int reps, void *stream,
                                  sg_tuning *best, double *best_ms) {
     if (!best || reps < 1) return SG_EINVAL;
-    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    if (!prec_ok(prec)) return SG_EINVAL;
     sg_tuning saved;
     ST(sg_get_tuning(prec, &saved));
     const int ppc[] = {2048, 8192, 32768, 131072};
@@ -905,7 +917,7 @@ extern "C" sg_status sg_profile_end(void *stream, double *fold_ms, int *launches
 }
 
 extern "C" sg_status sg_ceiling(sg_precision prec, int kind, void *stream, double *rate) {
-    if (!rate || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) || kind < 0 || kind > 2)
+    if (!rate || !prec_ok(prec) || kind < 0 || kind > 2)
         return SG_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
     cudaGetLastError();  // a failed earlier call must not surface here
@@ -934,7 +946,7 @@ extern "C" sg_status sg_ceiling(sg_precision prec, int kind, void *stream, doubl
 extern "C" sg_status sg_eval_functions(int kind, sg_precision prec, const double *d_x, double *d_y, int n,
                                        void *stream) {
     if (!d_x || !d_y || n < 0 || kind < 0 || kind > 1) return SG_EINVAL;
-    if (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED) return SG_EINVAL;
+    if (!prec_ok(prec)) return SG_EINVAL;
     cudaGetLastError();
     CK(sg_launch_fn(kind, prec, d_x, d_y, n, (cudaStream_t)stream));
     return SG_OK;

@@ -28,6 +28,9 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <type_traits>
+
+#include "sg_ff.cuh"
 #include "sg_fold_logic.h"
 #include "sg_kernels.h"
 
@@ -89,9 +92,14 @@ __device__ __forceinline__ double phi_centre(int fam, double a, double u) {
     return 0.0;
 }
 
+// Float-float precision tag: table entries and prefix states are float4
+// (value hi, lo, weight hi, lo).
+struct FFTag {};
+
 template <typename T> struct V2T;
 template <> struct V2T<float> { typedef float2 type; };
 template <> struct V2T<double> { typedef double2 type; };
+template <> struct V2T<FFTag> { typedef float4 type; };
 
 // expm1 in float for the fold's argument range (no special-case paths): Cody & Waite argument reduction x = k ln2 + r, |r| <= ln2/2,
 // with ln 2 split so that k * ln2_hi is exact, the Taylor series of
@@ -136,6 +144,18 @@ template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double H, 
     return sh * fma(sphi, ch, cphi * sh);
 }
 
+// Float-float deviation (see sg_ff.cuh): expm1, or for the oscillatory kind
+// sin(H) sin(phi + H) = sin(H) (sin(phi) cos(H) + cos(phi) sin(H)).
+template <int GK> __device__ __forceinline__ ff2 gdev_ff(ff2 S, ff2 sphi, ff2 cphi) {
+    if constexpr (GK == SG_GK_EXPM1) {
+        return ff_expm1(S);
+    } else {
+        ff2 sh, ch;
+        ff_sincos(S, &sh, &ch);
+        return ff_mul(sh, ff_add(ff_mul(sphi, ch), ff_mul(cphi, sh)));
+    }
+}
+
 // Weight factor of the deviation kind (see gdev).
 template <int GK> __device__ __forceinline__ double gdev_weight() { return GK == SG_GK_OSC ? -2.0 : 1.0; }
 
@@ -162,12 +182,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 struct FoldAcc {
     double acc = 0.0;
     float hs = 0.f, hc = 0.f, habs = 0.f;
+    ff2 fa = {0.f, 0.f};  // float-float path
 };
 
 // Prefix state of one prefix node tuple: partial argument S and weight W.
 template <typename T> struct PrefixState;
 template <> struct PrefixState<float> { typedef float2 type; };
 template <> struct PrefixState<double> { typedef double2 type; };
+template <> struct PrefixState<FFTag> { typedef float4 type; };
 
 // Folds the points (prefix tuple a < At) x (tail entries e < E1 + E2) of one
 // run.  Tail entries come from up to two contiguous table segments (two
@@ -231,6 +253,35 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
     }
 }
 
+// Float-float fold of one run (same lane layout as fold_run).
+template <int GK>
+__device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long long base1, int E1,
+                                            long long base2, int E2, const float4 *sP, int At, ff2 sphi,
+                                            ff2 cphi, int lane, FoldAcc &F) {
+    const int E = E1 + E2;
+    const int G = E >= 32 ? 1 : 32 / E;
+    const int Eg = E >= 32 ? 32 : E;
+    const int sub = lane / Eg, el = lane - sub * Eg;
+    if (sub >= G) return;
+    ff2 fa = F.fa;
+    float habs = F.habs;
+    for (int e0 = 0; e0 < E; e0 += Eg) {
+        const int e = e0 + el;
+        if (e >= E) break;
+        const float4 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
+        for (int a = sub; a < At; a += G) {
+            const float4 p = sP[a];
+            const ff2 S = ff_add(ff2{p.x, p.y}, ff2{te.x, te.y});
+            const ff2 W = ff_mul(ff2{p.z, p.w}, ff2{te.z, te.w});
+            const ff2 D = gdev_ff<GK>(S, sphi, cphi);
+            fa = ff_add(fa, ff_mul(W, D));
+            habs = fmaf(fabsf(W.hi), fabsf(D.hi), habs);
+        }
+    }
+    F.fa = fa;
+    F.habs = habs;
+}
+
 template <typename T, int GK>
 __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                            const SgItemDev *__restrict__ I, unsigned long long c,
@@ -239,7 +290,9 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
     const int d = I->d, r = P->r, skip = I->skip, tm = P->tm;
     const SgItemVar *V = A.vars + (I - A.items);
-    const T sphi = (T)V->sin_phi, cphi = (T)V->cos_phi;
+    typedef typename std::conditional<std::is_same<T, FFTag>::value, float, T>::type TS;
+    const TS sphi = (TS)V->sin_phi, cphi = (TS)V->cos_phi;
+    const ff2 ffsphi = ff_from_double(V->sin_phi), ffcphi = ff_from_double(V->cos_phi);
     unsigned long long rank, cnt;
     int a_lo, a_hi;
     sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
@@ -254,17 +307,30 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
             // fold the prefix directions: one state per prefix node tuple
             for (int a = lane; a < At; a += 32) {
                 int q = ab + a;
-                T S = 0, W = (T)gdev_weight<GK>();
-                for (int t = r - 2; t >= 0; t--) {
-                    const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
-                    S += e.x;
-                    W *= e.y;
+                if constexpr (std::is_same<T, FFTag>::value) {  // float-float
+                    ff2 S = {0.f, 0.f}, W = {(float)gdev_weight<GK>(), 0.f};
+                    for (int t = r - 2; t >= 0; t--) {
+                        const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
+                        S = ff_add(S, ff2{e.x, e.y});
+                        W = ff_mul(W, ff2{e.z, e.w});
+                    }
+                    sP[a] = make_float4(S.hi, S.lo, W.hi, W.lo);
+                } else {
+                    T S = 0, W = (T)gdev_weight<GK>();
+                    for (int t = r - 2; t >= 0; t--) {
+                        const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
+                        S += e.x;
+                        W *= e.y;
+                    }
+                    sP[a].x = S;
+                    sP[a].y = W;
                 }
-                sP[a].x = S;
-                sP[a].y = W;
             }
             __syncwarp();
-            fold_run<T, GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, sphi, cphi, lane, F);
+            if constexpr (std::is_same<T, FFTag>::value)
+                fold_run_ff<GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, ffsphi, ffcphi, lane, F);
+            else
+                fold_run<T, GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, sphi, cphi, lane, F);
             __syncwarp();
         }
         cnt -= run;
@@ -432,12 +498,12 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         FoldAcc F;
         if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sIdx, lane, F);
         else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sIdx, lane, F);
-        double acc = F.acc + ((double)F.hs + (double)F.hc), aabs = (double)F.habs;
+        double acc = F.acc + ((double)F.hs + (double)F.hc) + ff_to_double(F.fa), aabs = (double)F.habs;
         for (int o = 16; o > 0; o >>= 1) {
             acc += __shfl_xor_sync(FULL_MASK, acc, o);
             aabs += __shfl_xor_sync(FULL_MASK, aabs, o);
         }
-        if (sizeof(T) == 8) aabs = fabs(acc);  // the FP64 fold skips |W D| per point
+        if (std::is_same<T, double>::value) aabs = fabs(acc);  // the FP64 fold skips |W D| per point
         if (lane == 0) {
             SgSlot sl;
             sl.sum = acc * P->coef;
@@ -452,6 +518,7 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
 // no occupancy constraint (a few warps already saturate GB300's FP64 pipe).
 __global__ void __launch_bounds__(256, 4) sg_fold_kernel_f(SgFoldArgs A) { fold_kernel_body<float>(A); }
 __global__ void sg_fold_kernel_d(SgFoldArgs A) { fold_kernel_body<double>(A); }
+__global__ void __launch_bounds__(256, 2) sg_fold_kernel_x(SgFoldArgs A) { fold_kernel_body<FFTag>(A); }
 
 // ---------------------------------------------------------------------------
 // setup: per-integral base quantities and the (phi, w) tables
@@ -513,6 +580,10 @@ __global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
         const double phi = phi_table(G.fam, p[i], p[G.d + i], xw.x);
         if (A.tab64) A.tab64[B.off + local] = make_double2(phi, xw.y);
         if (A.tab32) A.tab32[B.off + local] = make_float2((float)phi, (float)xw.y);
+        if (A.tabff) {
+            const ff2 fp = ff_from_double(phi), fw = ff_from_double(xw.y);
+            A.tabff[B.off + local] = make_float4(fp.hi, fp.lo, fw.hi, fw.lo);
+        }
     }
 }
 
@@ -639,7 +710,7 @@ cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s) {
 }
 
 static size_t fold_smem(int prec, int warps) {
-    const size_t psz = prec ? sizeof(float2) : sizeof(double2);
+    const size_t psz = prec == 1 ? sizeof(float2) : (prec == 2 ? sizeof(float4) : sizeof(double2));
     return (size_t)warps * (SG_APAD * psz + SG_MAX_R * sizeof(int));
 }
 
@@ -647,7 +718,9 @@ int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
     (void)gk;
     int n = 0;
     const size_t sm = fold_smem(prec, warps_per_cta);
-    if (prec)
+    if (prec == 2)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_x, 32 * warps_per_cta, sm);
+    else if (prec == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_f, 32 * warps_per_cta, sm);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_d, 32 * warps_per_cta, sm);
@@ -657,7 +730,8 @@ int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
 cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cfg, cudaStream_t s) {
     (void)gk;
     const size_t sm = fold_smem(prec, cfg.warps_per_cta);
-    if (prec) sg_fold_kernel_f<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
+    if (prec == 2) sg_fold_kernel_x<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
+    else if (prec == 1) sg_fold_kernel_f<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
     else sg_fold_kernel_d<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
     return cudaGetLastError();
 }
@@ -736,7 +810,41 @@ __global__ void __launch_bounds__(256) sg_fma_kernel(int sweeps, double *out) {
     out[blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
 }
 
+// The float-float inner loop on register-resident data.
+template <int GK>
+__global__ void __launch_bounds__(256) sg_ceiling_ff_kernel(int sweeps, double *out) {
+    ff2 dl[4], wl[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        dl[k] = ff2{(float)((k - 1.5) * 0.05 + threadIdx.x * 1e-5), 1e-12f};
+        wl[k] = ff2{(k & 1) ? -0.25f : 0.3f, 1e-10f};
+    }
+    ff2 S = {(float)(blockIdx.x * 1e-6), 0.f}, W = {0.7f, 0.f};
+    const ff2 sphi = {0.3f, 0.f}, cphi = {0.95f, 0.f};
+    ff2 fa = {0.f, 0.f};
+    float habs = 0.f;
+    for (int it = 0; it < sweeps; it++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const ff2 s = ff_add(S, dl[k]), w = ff_mul(W, wl[k]);
+            const ff2 D = gdev_ff<GK>(s, sphi, cphi);
+            fa = ff_add(fa, ff_mul(w, D));
+            habs = fmaf(fabsf(w.hi), fabsf(D.hi), habs);
+        }
+        S = ff_add_f(S, 1e-7f);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = ff_to_double(fa) + 1e-30 * habs;
+}
+
 double sg_launch_ceiling(int prec, int kind, int sms, double *d_out, cudaStream_t s) {
+    if (prec == 2 && kind != 2) {
+        const int threads = 256, blocks = sms * 8;
+        const int sweeps = 1 << 9;
+        if (kind == 1) sg_ceiling_ff_kernel<SG_GK_OSC><<<blocks, threads, 0, s>>>(sweeps, d_out);
+        else sg_ceiling_ff_kernel<SG_GK_EXPM1><<<blocks, threads, 0, s>>>(sweeps, d_out);
+        return 4.0 * threads * (double)blocks * sweeps;
+    }
+    if (prec == 2) prec = 1;
     const int threads = 256, blocks = sms * 8;
     int sweeps;
     double per = 8.0 * threads * (double)blocks;
@@ -765,6 +873,18 @@ double sg_launch_ceiling(int prec, int kind, int sms, double *d_out, cudaStream_
 __global__ void sg_fn_kernel(int kind, int prec, const double *x, double *y, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (prec == 2) {
+        const ff2 a = ff_from_double(x[i]);
+        if (kind == 0) {
+            y[i] = ff_to_double(ff_expm1(a));
+        } else {
+            ff2 s, c;
+            ff_sincos(a, &s, &c);
+            y[2 * i] = ff_to_double(s);
+            y[2 * i + 1] = ff_to_double(c);
+        }
+        return;
+    }
     if (kind == 0) {
         y[i] = prec ? (double)sg_expm1f((float)x[i]) : expm1(x[i]);
     } else {

@@ -32,6 +32,7 @@ struct SgSetupArgs {
     const double *params;
     float2 *tab32;                // may be NULL
     double2 *tab64;               // may be NULL
+    float4 *tabff;                // float-float (value hi, lo, weight hi, lo); may be NULL
     SgBaseDev *bases;             // one per integral
     const int *flags;             // guard flags per item (NULL: build all)
 };
@@ -91,7 +92,7 @@ struct SgPrepArgs {
 };
 // Fills the per-call item values (phases, multipliers) after the setup kernel.
 cudaError_t sg_launch_prep(const SgPrepArgs &a, cudaStream_t s);
-// prec: 0 = double tables, 1 = float tables.
+// prec: 0 = double tables, 1 = float tables, 2 = float-float tables.
 cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cfg, cudaStream_t s);
 // Resident CTAs per SM of the fold kernel for this precision / warps per CTA.
 int sg_fold_occupancy(int prec, int gk, int warps_per_cta);

@@ -67,3 +67,24 @@ def test_double_sincos_accuracy():
     assert np.abs(c - rc).max() <= 4 * U64
     small = (np.abs(x) < 0.5) & (x != 0)
     assert (np.abs(s - rs)[small] / np.abs(rs[small])).max() <= 2 * U64
+
+
+def test_float_float_expm1():
+    x = np.concatenate([_args(-40.0, 40.0, n=50001), [1e-30, -1e-30, 5e-8, -5e-8]])
+    y = _eval(0, sg.PREC_FF, x)
+    ref = np.expm1(x)
+    rel = np.abs(y - ref) / np.maximum(np.abs(ref), 1e-300)
+    # a float pair holds the argument to 2^-49 |x|, which alone moves
+    # exp(x) by that much relative; the arithmetic adds about 1e-13
+    bound = 1e-13 + 2.0 ** -48 * np.abs(x)
+    assert np.all(rel <= bound), (rel.max(), x[np.argmax(rel / bound)])
+
+
+def test_float_float_sincos():
+    x = _args(-60.0, 60.0, n=50001)
+    y = _eval(1, sg.PREC_FF, x)
+    s, c = y[0::2], y[1::2]
+    assert np.abs(s - np.sin(x)).max() <= 2e-13
+    assert np.abs(c - np.cos(x)).max() <= 2e-13
+    small = (np.abs(x) < 0.5) & (x != 0)
+    assert (np.abs(s - np.sin(x))[small] / np.abs(np.sin(x[small]))).max() <= 1e-13
