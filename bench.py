@@ -26,6 +26,31 @@ sys.path.insert(0, ROOT)
 METRIC = "effective sparse-grid points/sec and s/integral at stated rel. error vs FP64 oracle"
 
 
+# DRAM bytes per launch of the timed fold kernel, from the ncu capture
+# summarised in profiles/sg_fold_kernel_d__cfg2_d12_gl_L6_oscillatory.txt.
+# Valid only for the kernel sources with this digest; otherwise reported as
+# null until the capture is taken again.
+_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (105216, "c132d557d8d933e8")}
+_KERNEL_SOURCES = ["paper_2210_14313_gb300/csrc/sg_kernels.cu", "paper_2210_14313_gb300/csrc/sg_fold_logic.h",
+                   "paper_2210_14313_gb300/csrc/sg_ff.cuh", "paper_2210_14313_gb300/csrc/sg_internal.h"]
+
+
+def _kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for p in _KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _fold_traffic(name, prec):
+    t = _FOLD_TRAFFIC.get(name)
+    if t is None or prec != 0 or t[1] != _kernel_digest():
+        return None
+    return t[0]
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -115,6 +140,17 @@ def _oracle_rate(c, budget_s=12.0):
     return pts * n / dt, n, dt
 
 
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the job's timed region ends with its
+    slowest rank); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -162,7 +198,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     c, prec = _workload(args.workload)
     if args.prec is not None:
-        prec = {"fp64": 0, "mixed": 1}[args.prec]
+        prec = {"fp64": 0, "mixed": 1, "ff": 2}[args.prec]
     d, L = c["d"], c["L"]
     q = d + L
     rule = sg.Rule(c["rule"], max_level=L + 1)
@@ -203,11 +239,7 @@ def run_gpu(args):
         dist.barrier()
     clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    tot_ms = sum(ms)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = t.item()
+    tot_ms = max_over_ranks(sum(ms), dist, torch.device("cuda", local))
     value = ws * pts * args.steps / (tot_ms * 1e-3)
 
     # end to end through the public blocking call, host buffers (pinned)
@@ -234,7 +266,8 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32-eval/f64-sum",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f32-eval/f64-sum", 2: "f32x2-eval/f64-sum"}[prec],
         "data": "synthetic (seeded SplitMix64 parameters)",
         "config": {"workload": c["name"], "d": d, "q": q,
                    "rule": {1: "trapezoid", 2: "clenshaw_curtis", 4: "gauss_legendre"}[c["rule"]],
@@ -245,7 +278,7 @@ def run_gpu(args):
                    "rel_err_vs_oracle": rel_err},
         "s_per_integral": tot_ms * 1e-3 / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gevals/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": _fold_traffic(c["name"], prec),
                      "peak_source": "measured per-point ceiling kernel (sg_ceiling), same run",
                      "fma_peak_tflops": fma_peak / 1e12},
         "e2e": e2e,
@@ -327,7 +360,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2")
-    ap.add_argument("--prec", default=None, choices=[None, "fp64", "mixed"])
+    ap.add_argument("--prec", default=None, choices=[None, "fp64", "mixed", "ff"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     args = ap.parse_args()

@@ -276,3 +276,19 @@ def test_autograd_function(rules):
     (3.0 * val).backward()
     _, g = sg.integrate_grad(rules[2], c["fam"], c["params"], c["d"], q)
     assert torch.allclose(p.grad.cpu(), torch.tensor(3.0 * g), rtol=0, atol=1e-15 * np.abs(g).max())
+
+
+def test_autotune_picks_a_grid_point_and_keeps_results(rules):
+    items = si.batch(n=12, seed=21, d_hi=40, L_hi=3)
+    specs, pool = _batch(items, rules)
+    saved = sg.get_tuning(sg.PREC_MIXED)
+    try:
+        best, ms = sg.autotune(specs, pool, prec=sg.PREC_MIXED, reps=1)
+        assert best[0] in (2048, 8192, 32768, 131072) and best[1] in (4, 8, 16) and best[2] in (4, 8)
+        assert ms > 0
+        assert sg.get_tuning(sg.PREC_MIXED) == best
+        res = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED)
+        for it, r in zip(items, res):
+            assert rel_err(r, oracle_value(it)) <= max(MIXED_TOL, 20 * r.err_est)
+    finally:
+        sg.set_tuning(sg.PREC_MIXED, *saved)
