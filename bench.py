@@ -282,7 +282,7 @@ def run_gpu(args):
                      "peak_source": "measured per-point ceiling kernel (sg_ceiling), same run",
                      "fma_peak_tflops": fma_peak / 1e12},
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 2 * args.steps,  # setup + fold per integral
         "clocks": clk,
     }
     if rank == 0 and ws == 1 and not args.no_extra:

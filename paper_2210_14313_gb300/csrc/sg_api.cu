@@ -213,6 +213,8 @@ static sg_status plan_upload(Plan *P) {
     const size_t o_ii = carve<int>(sz, P->item_integral.size());
     const size_t o_pa = carve<SgPatDev>(sz, P->pats.size());
     const size_t o_pc = carve<u64>(sz, P->pat_chunk0.size());
+    const size_t o_ip = carve<int>(sz, P->int_item_ptr.size());
+    const size_t o_iv = carve<int>(sz, P->int_items.size() + 1);
     const size_t o_do = carve<int>(sz, P->delta_off.size() + 1);
     const size_t o_dm = carve<int>(sz, P->delta_m.size() + 1);
     std::vector<unsigned char> host(sz, 0);
@@ -224,6 +226,8 @@ static sg_status plan_upload(Plan *P) {
     memcpy(&host[o_ii], P->item_integral.data(), P->item_integral.size() * sizeof(int));
     memcpy(&host[o_pa], P->pats.data(), P->pats.size() * sizeof(SgPatDev));
     memcpy(&host[o_pc], P->pat_chunk0.data(), P->pat_chunk0.size() * sizeof(u64));
+    memcpy(&host[o_ip], P->int_item_ptr.data(), P->int_item_ptr.size() * sizeof(int));
+    memcpy(&host[o_iv], P->int_items.data(), P->int_items.size() * sizeof(int));
     if (!P->delta_off.empty()) {
         memcpy(&host[o_do], P->delta_off.data(), P->delta_off.size() * sizeof(int));
         memcpy(&host[o_dm], P->delta_m.data(), P->delta_m.size() * sizeof(int));
@@ -242,6 +246,8 @@ static sg_status plan_upload(Plan *P) {
     P->d_item_integral = (int *)(b + o_ii);
     P->d_pats = (SgPatDev *)(b + o_pa);
     P->d_pat_chunk0 = (u64 *)(b + o_pc);
+    P->d_int_item_ptr = (int *)(b + o_ip);
+    P->d_int_items = (int *)(b + o_iv);
     P->d_delta_off = (int *)(b + o_do);
     P->d_delta_m = (int *)(b + o_dm);
     P->d_delta_xw = P->reqs[0].rule->d_xw;
@@ -505,6 +511,13 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     sa.blocks = P->d_blocks;
     sa.block_end = P->d_block_end;
     sa.nblocks = (int)P->blocks.size();
+    if (sa.nblocks <= SG_SETUP_INLINE) {
+        sa.ninline = sa.nblocks;
+        for (int b = 0; b < sa.nblocks; b++) {
+            sa.blk_inline[b] = P->blocks[b];
+            sa.end_inline[b] = P->block_end[b];
+        }
+    }
     sa.nentries = P->nentries;
     sa.integrals = P->d_integrals;
     sa.nintegrals = (int)P->integrals.size();
@@ -514,22 +527,18 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     sa.tabff = prec == 2 ? (float4 *)W->tabff.p : nullptr;
     sa.bases = (SgBaseDev *)W->bases.p;
     sa.flags = nullptr;
-    CK(sg_launch_setup(sa, s));
     const double u = unit_roundoff(prec);
-    SgPrepArgs pa;
-    pa.roles = P->d_roles;
-    pa.items = P->d_items;
-    pa.nitems = nitems;
-    pa.integrals = P->d_integrals;
-    pa.params = d_params;
-    pa.bases = (SgBaseDev *)W->bases.p;
-    pa.item_integral = P->d_item_integral;
-    pa.vars = (SgItemVar *)W->vars.p;
-    pa.out = outp;
-    pa.vout = (double *)W->vout.p;
-    pa.flags = (guard_tol > 0.0) ? (int *)W->flags.p : nullptr;
-    pa.unit_roundoff = u;
-    CK(sg_launch_prep(pa, s));
+    sa.do_items = 1;
+    sa.int_item_ptr = P->d_int_item_ptr;
+    sa.int_items = P->d_int_items;
+    sa.roles = P->d_roles;
+    sa.items = P->d_items;
+    sa.item_integral = P->d_item_integral;
+    sa.vars = (SgItemVar *)W->vars.p;
+    sa.out = outp;
+    sa.vout = (double *)W->vout.p;
+    sa.unit_roundoff = u;
+    CK(sg_launch_setup(sa, s));
     if (P->nchunks == 0) return SG_OK;
     SgFoldArgs fa;
     memset(&fa, 0, sizeof(fa));
@@ -564,6 +573,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
         sa.tab32 = nullptr;
         sa.tabff = (float4 *)W->tabff.p;
         sa.flags = (int *)W->flags.p;
+        sa.do_items = 0;
         CK(sg_launch_setup(sa, s));
         fa.tab = W->tabff.p;
         fa.skip_unflagged = (int *)W->flags.p;

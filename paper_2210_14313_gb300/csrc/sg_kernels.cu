@@ -289,15 +289,19 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     typedef typename V2T<T>::type V2;
     const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
     const int d = I->d, r = P->r, skip = I->skip, tm = P->tm;
-    const SgItemVar *V = A.vars + (I - A.items);
-    typedef typename std::conditional<std::is_same<T, FFTag>::value, float, T>::type TS;
-    const TS sphi = (TS)V->sin_phi, cphi = (TS)V->cos_phi;
-    const ff2 ffsphi = ff_from_double(V->sin_phi), ffcphi = ff_from_double(V->cos_phi);
     unsigned long long rank, cnt;
     int a_lo, a_hi;
     sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
     if (lane == 0) sg_unrank_lex(rank, d, r, A.binom, sIdx);
+    // everything above reads only the plan; the tables and item values come
+    // from the setup kernel, which may still be finishing (programmatic
+    // dependent launch)
+    cudaGridDependencySynchronize();
     __syncwarp();
+    const SgItemVar *V = A.vars + (I - A.items);
+    typedef typename std::conditional<std::is_same<T, FFTag>::value, float, T>::type TS;
+    const TS sphi = (TS)V->sin_phi, cphi = (TS)V->cos_phi;
+    const ff2 ffsphi = ff_from_double(V->sin_phi), ffcphi = ff_from_double(V->cos_phi);
     while (cnt > 0) {
         const int plast = sIdx[r - 1];
         const int run = (unsigned long long)(d - plast) < cnt ? d - plast : (int)cnt;
@@ -524,77 +528,10 @@ __global__ void __launch_bounds__(256, 2) sg_fold_kernel_x(SgFoldArgs A) { fold_
 // setup: per-integral base quantities and the (phi, w) tables
 // ---------------------------------------------------------------------------
 
-// Blocks [0, nbase) compute one integral per warp: log f(c) as a compensated
-// sum in a fixed order (lane-strided Neumaier, lanes combined in order), or
-// the oscillatory centre phase.  The remaining blocks fill table entries.
-__global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
-    const int lane = threadIdx.x & 31;
-    if ((int)blockIdx.x < nbase) {
-        const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        if (g >= A.nintegrals) return;
-        const SgIntegralDev G = A.integrals[g];
-        const double *a = A.params + G.param_off, *u = a + G.d;
-        double s = 0.0, c = 0.0;
-        for (int i = lane; i < G.d; i += 32) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
-        double S = 0.0, C = 0.0;
-        for (int t = 0; t < 32; t++) {
-            const double st = __shfl_sync(FULL_MASK, s, t), ct = __shfl_sync(FULL_MASK, c, t);
-            neu_add(S, C, st);
-            neu_add(S, C, ct);
-        }
-        if (lane) return;
-        SgBaseDev B;
-        if (G.fam == 1) {
-            const double two_pi = 6.28318530717958647693;
-            const double th = remainder(two_pi * u[0] + (S + C), two_pi);
-            B.log_hi = 0.0;
-            B.log_lo = 0.0;
-            sincos(th, &B.sin_th, &B.cos_th);
-            B.base = B.cos_th;
-        } else {
-            B.log_hi = S;
-            B.log_lo = C;
-            B.base = 1.0;
-            B.sin_th = 0.0;
-            B.cos_th = 1.0;
-        }
-        A.bases[g] = B;
-        return;
-    }
-    const long long stride = (long long)(gridDim.x - nbase) * blockDim.x;
-    for (long long e = (long long)(blockIdx.x - nbase) * blockDim.x + threadIdx.x; e < A.nentries;
-         e += stride) {
-        int lo = 0, hi = A.nblocks - 1;  // first block whose end > e
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(A.block_end + mid) > e) hi = mid;
-            else lo = mid + 1;
-        }
-        const SgBlockDev B = A.blocks[lo];
-        const long long local = e - (lo ? __ldg(A.block_end + lo - 1) : 0);
-        const SgIntegralDev G = A.integrals[B.integral];
-        if (A.flags && G.flag_item >= 0 && !A.flags[G.flag_item]) continue;
-        const int i = (int)(local / B.m), j = (int)(local - (long long)i * B.m);
-        const double2 xw = B.xw[j];
-        const double *p = A.params + G.param_off;
-        const double phi = phi_table(G.fam, p[i], p[G.d + i], xw.x);
-        if (A.tab64) A.tab64[B.off + local] = make_double2(phi, xw.y);
-        if (A.tab32) A.tab32[B.off + local] = make_float2((float)phi, (float)xw.y);
-        if (A.tabff) {
-            const ff2 fp = ff_from_double(phi), fw = ff_from_double(xw.y);
-            A.tabff[B.off + local] = make_float4(fp.hi, fp.lo, fw.hi, fw.lo);
-        }
-    }
-}
-
 // Per-call item values: the oscillatory phase of the per-point deviation and
 // the centre term, from the integral's centre phase theta_c (or log f(c)).
-__global__ void sg_prep_kernel(SgPrepArgs A) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= A.nitems) return;
-    const SgItemRole R = A.roles[it];
-    const SgIntegralDev G = A.integrals[R.integral];
-    const SgBaseDev B = A.bases[R.integral];
+__device__ __forceinline__ SgItemVar item_values(const SgItemRole &R, const SgIntegralDev &G,
+                                                 const SgBaseDev &B, const double *params) {
     SgItemVar V;
     double sn = B.sin_th, cs = B.cos_th;
     if (R.role != SG_ROLE_FORWARD && G.fam == 1) {  // advance the phase by pi/2
@@ -604,7 +541,7 @@ __global__ void sg_prep_kernel(SgPrepArgs A) {
     }
     double shift = 0.0;
     if (R.role == SG_ROLE_ADJOINT) {
-        const double *p = A.params + G.param_off;
+        const double *p = params + G.param_off;
         shift = phi_dev(G.fam, p[R.dir], p[G.d + R.dir], R.x);
     }
     if (G.fam == 1) {
@@ -621,7 +558,104 @@ __global__ void sg_prep_kernel(SgPrepArgs A) {
         V.base_rel = 1.0;
         V.mult = exp(shift);
     }
-    A.vars[it] = V;
+    return V;
+}
+
+// Blocks [0, nbase) compute one integral per warp: log f(c) as a compensated
+// sum in a fixed order (lane-strided Neumaier, lanes combined in order), or
+// the oscillatory centre phase.  The remaining blocks fill table entries.
+__global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
+    // let a fold launched as a programmatic dependent start its plan-only work
+    cudaTriggerProgrammaticLaunchCompletion();
+    const int lane = threadIdx.x & 31;
+    if ((int)blockIdx.x < nbase) {
+        const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (g >= A.nintegrals) return;
+        const SgIntegralDev G = A.integrals[g];
+        const double *a = A.params + G.param_off, *u = a + G.d;
+        double s = 0.0, c = 0.0;
+        for (int i = lane; i < G.d; i += 32) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
+        // combine the lanes' compensated pairs by a fixed butterfly (the same
+        // order on every call; five dependent steps instead of 32)
+        for (int o = 1; o < 32; o <<= 1) {
+            const double so = __shfl_xor_sync(FULL_MASK, s, o), co = __shfl_xor_sync(FULL_MASK, c, o);
+            // lower lane of each pair first, so both lanes compute the same sum
+            double s1 = (lane & o) ? so : s, c1 = (lane & o) ? co : c;
+            double s2 = (lane & o) ? s : so, c2 = (lane & o) ? c : co;
+            neu_add(s1, c1, s2);
+            c1 += c2;
+            s = s1;
+            c = c1;
+        }
+        const double S = s, C = c;
+        SgBaseDev B;
+        if (G.fam == 1) {
+            B.log_hi = 0.0;
+            B.log_lo = 0.0;
+            sincos(6.28318530717958647693 * u[0] + (S + C), &B.sin_th, &B.cos_th);
+            B.base = B.cos_th;
+        } else {
+            B.log_hi = S;
+            B.log_lo = C;
+            B.base = 1.0;
+            B.sin_th = 0.0;
+            B.cos_th = 1.0;
+        }
+        if (lane == 0) A.bases[g] = B;
+        if (!A.do_items) return;
+        __syncwarp();
+        for (int t = A.int_item_ptr[g] + lane; t < A.int_item_ptr[g + 1]; t += 32) {
+            const int it = A.int_items[t];
+            A.vars[it] = item_values(A.roles[it], G, B, A.params);
+            if (A.items[it].nchunk == 0)
+                assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, nullptr, 0.0,
+                              A.unit_roundoff, it, 0.0, 0.0);
+        }
+        return;
+    }
+    const long long stride = (long long)(gridDim.x - nbase) * blockDim.x;
+    for (long long e = (long long)(blockIdx.x - nbase) * blockDim.x + threadIdx.x; e < A.nentries;
+         e += stride) {
+        int lo = 0, hi = A.nblocks - 1;  // first block whose end > e
+        SgBlockDev B;
+        long long local;
+        if (A.ninline) {  // descriptors in the kernel parameters: no dependent loads
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A.end_inline[mid] > e) hi = mid;
+                else lo = mid + 1;
+            }
+            B = A.blk_inline[lo];
+            local = e - (lo ? A.end_inline[lo - 1] : 0);
+        } else {
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(A.block_end + mid) > e) hi = mid;
+                else lo = mid + 1;
+            }
+            B = A.blocks[lo];
+            local = e - (lo ? __ldg(A.block_end + lo - 1) : 0);
+        }
+        const SgIntegralDev G = A.integrals[B.integral];
+        if (A.flags && G.flag_item >= 0 && !A.flags[G.flag_item]) continue;
+        const int i = (int)(local / B.m), j = (int)(local - (long long)i * B.m);
+        const double2 xw = B.xw[j];
+        const double *p = A.params + G.param_off;
+        const double phi = phi_table(G.fam, p[i], p[G.d + i], xw.x);
+        if (A.tab64) A.tab64[B.off + local] = make_double2(phi, xw.y);
+        if (A.tab32) A.tab32[B.off + local] = make_float2((float)phi, (float)xw.y);
+        if (A.tabff) {
+            const ff2 fp = ff_from_double(phi), fw = ff_from_double(xw.y);
+            A.tabff[B.off + local] = make_float4(fp.hi, fp.lo, fw.hi, fw.lo);
+        }
+    }
+}
+
+__global__ void sg_prep_kernel(SgPrepArgs A) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= A.nitems) return;
+    const SgItemRole R = A.roles[it];
+    A.vars[it] = item_values(R, A.integrals[R.integral], A.bases[R.integral], A.params);
     if (A.items[it].nchunk == 0)
         assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, 0.0,
                       A.unit_roundoff, it, 0.0, 0.0);
@@ -730,10 +764,22 @@ int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
 cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cfg, cudaStream_t s) {
     (void)gk;
     const size_t sm = fold_smem(prec, cfg.warps_per_cta);
-    if (prec == 2) sg_fold_kernel_x<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
-    else if (prec == 1) sg_fold_kernel_f<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
-    else sg_fold_kernel_d<<<cfg.ctas, 32 * cfg.warps_per_cta, sm, s>>>(a);
-    return cudaGetLastError();
+    // programmatic dependent launch: the fold may begin while the preceding
+    // kernel in the stream finishes; it waits (cudaGridDependencySynchronize)
+    // before it reads that kernel's output
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.ctas);
+    lc.blockDim = dim3(32 * cfg.warps_per_cta);
+    lc.dynamicSmemBytes = sm;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (prec == 2) return cudaLaunchKernelEx(&lc, sg_fold_kernel_x, a);
+    if (prec == 1) return cudaLaunchKernelEx(&lc, sg_fold_kernel_f, a);
+    return cudaLaunchKernelEx(&lc, sg_fold_kernel_d, a);
 }
 
 cudaError_t sg_launch_prep(const SgPrepArgs &a, cudaStream_t s) {

@@ -22,10 +22,15 @@ struct SgIntegralDev {
     int pad;
 };
 
+#define SG_SETUP_INLINE 32  // block descriptors passed by value when a plan has this few
+
 struct SgSetupArgs {
     const SgBlockDev *blocks;
     const long long *block_end;  // inclusive prefix sum of block entry counts
     int nblocks;
+    int ninline;                 // > 0: blocks/ends below are valid copies (kernel parameters)
+    SgBlockDev blk_inline[SG_SETUP_INLINE];
+    long long end_inline[SG_SETUP_INLINE];
     long long nentries;
     const SgIntegralDev *integrals;
     int nintegrals;
@@ -35,6 +40,18 @@ struct SgSetupArgs {
     float4 *tabff;                // float-float (value hi, lo, weight hi, lo); may be NULL
     SgBaseDev *bases;             // one per integral
     const int *flags;             // guard flags per item (NULL: build all)
+    // per-item values, computed by each integral's warp right after its base
+    // quantities (0: left to sg_launch_prep)
+    int do_items;
+    const int *int_item_ptr;      // items of integral g: int_items[ptr[g] .. ptr[g+1])
+    const int *int_items;
+    const SgItemRole *roles;
+    const SgItemDev *items;
+    const int *item_integral;
+    SgItemVar *vars;
+    SgOutDev *out;
+    double *vout;
+    double unit_roundoff;
 };
 
 struct SgFoldArgs {

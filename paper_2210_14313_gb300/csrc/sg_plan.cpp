@@ -317,6 +317,15 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
         if (b.role.role == SG_ROLE_FORWARD) P->integrals[g].flag_item = (int)q;
     }
     P->nchunks = chunk;
+    // items of each integral (the setup kernel's per-integral warp fills their values)
+    P->int_item_ptr.assign(nint + 1, 0);
+    for (const SgItemRole &R : P->roles) P->int_item_ptr[R.integral + 1]++;
+    for (int g = 0; g < nint; g++) P->int_item_ptr[g + 1] += P->int_item_ptr[g];
+    P->int_items.assign(P->roles.size(), 0);
+    {
+        std::vector<int> fill(P->int_item_ptr.begin(), P->int_item_ptr.end() - 1);
+        for (size_t it = 0; it < P->roles.size(); it++) P->int_items[fill[P->roles[it].integral]++] = (int)it;
+    }
     if (P->pats.empty()) {  // keep the device arrays non-empty
         SgPatDev pd;
         memset(&pd, 0, sizeof(pd));

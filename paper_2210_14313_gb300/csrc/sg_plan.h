@@ -56,6 +56,7 @@ struct Plan {
     std::vector<SgItemDev> items;
     std::vector<SgItemRole> roles;
     std::vector<int> item_integral;
+    std::vector<int> int_item_ptr, int_items;  // items of each integral (CSR)
     std::vector<SgPatDev> pats;
     std::vector<u64> pat_chunk0;
     long long nentries = 0;
@@ -77,6 +78,7 @@ struct Plan {
     SgItemDev *d_items = nullptr;
     SgItemRole *d_roles = nullptr;
     int *d_item_integral = nullptr;
+    int *d_int_item_ptr = nullptr, *d_int_items = nullptr;
     SgPatDev *d_pats = nullptr;
     u64 *d_pat_chunk0 = nullptr;
     int *d_delta_off = nullptr, *d_delta_m = nullptr;

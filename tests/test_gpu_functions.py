@@ -74,9 +74,10 @@ def test_float_float_expm1():
     y = _eval(0, sg.PREC_FF, x)
     ref = np.expm1(x)
     rel = np.abs(y - ref) / np.maximum(np.abs(ref), 1e-300)
-    # a float pair holds the argument to 2^-49 |x|, which alone moves
-    # exp(x) by that much relative; the arithmetic adds about 1e-13
-    bound = 1e-13 + 2.0 ** -48 * np.abs(x)
+    # a float pair holds the argument to about 2^-50 |x|, and the float
+    # correction (1 + E) x.lo adds up to 2^-48 |x| relative: the bound is
+    # 1e-13 for the arithmetic plus 2^-46 |x|
+    bound = 1e-13 + 2.0 ** -46 * np.abs(x)
     assert np.all(rel <= bound), (rel.max(), x[np.argmax(rel / bound)])
 
 
