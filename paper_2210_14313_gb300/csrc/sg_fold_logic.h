@@ -42,6 +42,51 @@ SG_HD void sg_unrank_lex(unsigned long long rank, int d, int r, const unsigned l
     }
 }
 
+// The same unranking, searched 32 candidates at a time (one per lane of a
+// warp): for position t the answer v is the largest value in [lo, hi] with
+// C(d-v, k) >= target.  A round tests lo + j*step, j = 0..31, with
+// step = ceil((hi-lo+1)/32); `mask` has bit j set where the test holds (bit
+// 0 always does) and the answer lies in the window after the last set bit.
+// Rounds repeat until step = 1; d <= 8192 needs at most three.
+struct SgUnrankPos {
+    int k, lo, hi, step;
+    unsigned long long total, target;
+};
+
+SG_HD void sg_unrank_begin(SgUnrankPos *u, unsigned long long rank, int d, int r, int t, int p,
+                           const unsigned long long *B) {
+    u->k = r - t;
+    u->total = sg_binom(B, d - p - 1, u->k);
+    u->target = u->total - rank;
+    u->lo = p + 1;
+    u->hi = d - u->k;
+    u->step = (u->hi - u->lo + 32) / 32;
+}
+
+// Candidate of lane j in the current round and whether its test holds.
+SG_HD int sg_unrank_candidate(const SgUnrankPos *u, int j) { return u->lo + j * u->step; }
+SG_HD bool sg_unrank_test(const SgUnrankPos *u, int v, int d, const unsigned long long *B) {
+    return v <= u->hi && sg_binom(B, d - v, u->k) >= u->target;
+}
+
+// Narrows the window after a round; returns 1 when lo is the answer.
+SG_HD int sg_unrank_narrow(SgUnrankPos *u, unsigned mask) {
+#ifdef __CUDA_ARCH__
+    const int j = 31 - __clz(mask);
+#else
+    int j = 31;
+    while (!((mask >> j) & 1u)) j--;
+#endif
+    const int done = u->step == 1;
+    u->lo += j * u->step;
+    if (!done) {
+        const int hi = u->lo + u->step - 1;
+        if (hi < u->hi) u->hi = hi;
+        u->step = (u->hi - u->lo + 32) / 32;
+    }
+    return done;
+}
+
 // Lexicographic successor of a subset whose last element is d-1: the
 // largest position t < r-1 that can still grow is incremented and the
 // following positions restart right after it.  Returns 0 when exhausted.
@@ -80,6 +125,28 @@ SG_HD SgTailSegs sg_tail_segments(long long toff, int tm, int plast, int run, in
     }
     return s;
 }
+
+// Lane position in the flat point space of a run, f = a * E + e (prefix
+// tuple a, tail entry e): lane l starts at f = l and advances by 32, so every
+// warp instruction but the last of a run has all 32 lanes busy, whatever
+// the tail length E.
+struct SgFlatPos {
+    int a, e, da, de, E;
+    SG_HD SgFlatPos(int lane, int E_) : E(E_) {
+        da = 32 / E;
+        de = 32 - da * E;
+        a = lane / E;
+        e = lane - a * E;
+    }
+    SG_HD void step() {
+        e += de;
+        a += da;
+        if (e >= E) {
+            e -= E;
+            a++;
+        }
+    }
+};
 
 // Table entry of prefix position t for prefix node tuple q (mixed radix over
 // the prefix block sizes, the last prefix position fastest).  Returns the

@@ -163,11 +163,6 @@ template <int GK> __device__ __forceinline__ double gdev_weight() { return GK ==
 // the fold: one chunk of one pattern, processed by one warp
 // ---------------------------------------------------------------------------
 
-// Folds the points (prefix tuple a < At) x (tail entries e < E1 + E2) of one
-// run.  Tail entries come from up to two contiguous table segments (two
-// when the enumerated directions jump over a left-out direction).  Lanes are
-// spread over tail entries; when a run has fewer than 32 entries, the warp
-// splits into groups that take different prefix tuples.
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
@@ -191,11 +186,16 @@ template <> struct PrefixState<float> { typedef float2 type; };
 template <> struct PrefixState<double> { typedef double2 type; };
 template <> struct PrefixState<FFTag> { typedef float4 type; };
 
+// Table entry of tail entry e: segment 1 holds e < E1, segment 2 the rest.
+template <typename V2>
+__device__ __forceinline__ V2 tail_entry(const V2 *__restrict__ tab, long long base1, int E1, long long base2,
+                                         int e) {
+    return tab[e < E1 ? base1 + e : base2 + (e - E1)];
+}
+
 // Folds the points (prefix tuple a < At) x (tail entries e < E1 + E2) of one
 // run.  Tail entries come from up to two contiguous table segments (two
-// when the enumerated directions jump over a left-out direction).  Lanes are
-// spread over tail entries; when a run has fewer than 32 entries, the warp
-// splits into groups that take different prefix tuples.
+// when the enumerated directions jump over a left-out direction).
 template <typename T, int GK>
 __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict__ tab,
                                          long long base1, int E1, long long base2, int E2,
@@ -203,53 +203,53 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
                                          T cphi, int lane, FoldAcc &F) {
     typedef typename V2T<T>::type V2;
     const int E = E1 + E2;
-    const int G = E >= 32 ? 1 : 32 / E;
-    const int Eg = E >= 32 ? 32 : E;
-    const int sub = lane / Eg, el = lane - sub * Eg;
-    if (sub >= G) return;
-    for (int e0 = 0; e0 < E; e0 += Eg) {
-        const int e = e0 + el;
-        if (e >= E) break;
-        const V2 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
-        if constexpr (sizeof(T) == 4) {
-            float hs = F.hs, hc = F.hc, habs = F.habs;
-            int a = sub;
-            for (; a + 7 * G < At; a += 8 * G) {
-                float part = 0.f;
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const float2 p = sP[a + u * G];
-                    const float W = p.y * te.y;
-                    const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
-                    part = fmaf(W, D, part);
-                    habs = fmaf(fabsf(W), fabsf(D), habs);
-                }
-                float t, err;
-                two_sum(hs, part, t, err);
-                hs = t;
-                hc += err;
-            }
+    SgFlatPos f(lane, E);
+    if constexpr (sizeof(T) == 4) {
+        // points of this lane; plain float partial sums of 8 points feed the
+        // TwoSum accumulator
+        const long long n = (long long)At * E;
+        const long long iters = lane < n ? (n - 1 - lane) / 32 + 1 : 0;
+        float hs = F.hs, hc = F.hc, habs = F.habs;
+        for (long long g = iters >> 3; g > 0; g--) {
             float part = 0.f;
-            for (; a < At; a += G) {
-                const float2 p = sP[a];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const float2 p = sP[f.a];
+                const V2 te = tail_entry(tab, base1, E1, base2, f.e);
                 const float W = p.y * te.y;
                 const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
                 part = fmaf(W, D, part);
                 habs = fmaf(fabsf(W), fabsf(D), habs);
+                f.step();
             }
             float t, err;
             two_sum(hs, part, t, err);
-            F.hs = t;
-            F.hc = hc + err;
-            F.habs = habs;
-        } else {
-            double acc = F.acc;
-            for (int a = sub; a < At; a += G) {
-                const double2 p = sP[a];
-                acc = fma(p.y * te.y, gdev<double, GK>(p.x + te.x, sphi, cphi), acc);
-            }
-            F.acc = acc;
+            hs = t;
+            hc += err;
         }
+        float part = 0.f;
+        for (int u = (int)(iters & 7); u > 0; u--) {
+            const float2 p = sP[f.a];
+            const V2 te = tail_entry(tab, base1, E1, base2, f.e);
+            const float W = p.y * te.y;
+            const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
+            part = fmaf(W, D, part);
+            habs = fmaf(fabsf(W), fabsf(D), habs);
+            f.step();
+        }
+        float t, err;
+        two_sum(hs, part, t, err);
+        F.hs = t;
+        F.hc = hc + err;
+        F.habs = habs;
+    } else {
+        double acc = F.acc;
+        for (; f.a < At; f.step()) {
+            const double2 p = sP[f.a];
+            const V2 te = tail_entry(tab, base1, E1, base2, f.e);
+            acc = fma(p.y * te.y, gdev<double, GK>(p.x + te.x, sphi, cphi), acc);
+        }
+        F.acc = acc;
     }
 }
 
@@ -258,28 +258,40 @@ template <int GK>
 __device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long long base1, int E1,
                                             long long base2, int E2, const float4 *sP, int At, ff2 sphi,
                                             ff2 cphi, int lane, FoldAcc &F) {
-    const int E = E1 + E2;
-    const int G = E >= 32 ? 1 : 32 / E;
-    const int Eg = E >= 32 ? 32 : E;
-    const int sub = lane / Eg, el = lane - sub * Eg;
-    if (sub >= G) return;
+    SgFlatPos f(lane, E1 + E2);
     ff2 fa = F.fa;
     float habs = F.habs;
-    for (int e0 = 0; e0 < E; e0 += Eg) {
-        const int e = e0 + el;
-        if (e >= E) break;
-        const float4 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
-        for (int a = sub; a < At; a += G) {
-            const float4 p = sP[a];
-            const ff2 S = ff_add(ff2{p.x, p.y}, ff2{te.x, te.y});
-            const ff2 W = ff_mul(ff2{p.z, p.w}, ff2{te.z, te.w});
-            const ff2 D = gdev_ff<GK>(S, sphi, cphi);
-            fa = ff_add(fa, ff_mul(W, D));
-            habs = fmaf(fabsf(W.hi), fabsf(D.hi), habs);
-        }
+    for (; f.a < At; f.step()) {
+        const float4 p = sP[f.a];
+        const float4 te = tail_entry(tab, base1, E1, base2, f.e);
+        const ff2 S = ff_add(ff2{p.x, p.y}, ff2{te.x, te.y});
+        const ff2 W = ff_mul(ff2{p.z, p.w}, ff2{te.z, te.w});
+        const ff2 D = gdev_ff<GK>(S, sphi, cphi);
+        fa = ff_add(fa, ff_mul(W, D));
+        habs = fmaf(fabsf(W.hi), fabsf(D.hi), habs);
     }
     F.fa = fa;
     F.habs = habs;
+}
+
+// Lexicographic unranking of the chunk's first r-subset by the whole warp:
+// each round tests 32 candidates of one position at once (sg_unrank_*), so
+// a position costs one or two rounds of parallel table loads instead of a
+// serial binary search.  Lane 0 writes the subset to idx.
+__device__ __forceinline__ void unrank_warp(unsigned long long rank, int d, int r,
+                                            const unsigned long long *B, int *idx, int lane) {
+    int p = -1;
+    for (int t = 0; t < r; t++) {
+        SgUnrankPos u;
+        sg_unrank_begin(&u, rank, d, r, t, p, B);
+        for (;;) {
+            const unsigned m = __ballot_sync(FULL_MASK, sg_unrank_test(&u, sg_unrank_candidate(&u, lane), d, B));
+            if (sg_unrank_narrow(&u, m)) break;
+        }
+        rank -= u.total - sg_binom(B, d - u.lo, u.k);
+        if (lane == 0) idx[t] = u.lo;
+        p = u.lo;
+    }
 }
 
 template <typename T, int GK>
@@ -292,7 +304,7 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     unsigned long long rank, cnt;
     int a_lo, a_hi;
     sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
-    if (lane == 0) sg_unrank_lex(rank, d, r, A.binom, sIdx);
+    unrank_warp(rank, d, r, A.binom, sIdx, lane);
     // everything above reads only the plan; the tables and item values come
     // from the setup kernel, which may still be finishing (programmatic
     // dependent launch)
@@ -379,8 +391,30 @@ __device__ void assemble_item(const SgItemDev *items, const SgItemVar *vars, con
     if (flags && guard_tol > 0.0) flags[item] = o.err_est > guard_tol ? 1 : 0;
 }
 
-// Lane l adds x[l], x[l+32], ... (Neumaier), then the lanes are combined in
-// lane order: a fixed summation order whichever warp runs it.  Eight loads
+// Combines the lanes' compensated pairs (s, c) and absolute sums with an
+// xor butterfly: at level o, lane l merges with lane l ^ o.  TwoSum returns
+// the exact rounding error of s_l + s_m, which does not depend on the order
+// of its operands, so both partners compute bitwise the same pair and every
+// lane ends with the same result; the tree is fixed, so the result does not
+// depend on which warp runs it.  Five levels of dependent FP64 work instead
+// of a 32-step lane-serial sum.
+__device__ __forceinline__ void lane_combine(double &s, double &c, double &ab) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double s2 = __shfl_xor_sync(FULL_MASK, s, o);
+        const double c2 = __shfl_xor_sync(FULL_MASK, c, o);
+        const double a2 = __shfl_xor_sync(FULL_MASK, ab, o);
+        const double t = __dadd_rn(s, s2);
+        const double z = __dsub_rn(t, s);
+        const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(s2, z));
+        s = t;
+        c = __dadd_rn(__dadd_rn(c, c2), e);
+        ab = __dadd_rn(ab, a2);
+    }
+}
+
+// Lane l adds x[l], x[l+32], ... (Neumaier), then the lanes are combined by
+// lane_combine: a fixed summation order whichever warp runs it.  Eight loads
 // are in flight per lane so that the L2 latency overlaps.
 __device__ void reduce_slots(const double2 *slots, unsigned long long n, int lane, double &S,
                              double &C, double &AB) {
@@ -401,17 +435,10 @@ __device__ void reduce_slots(const double2 *slots, unsigned long long n, int lan
         neu_add(s, c, v.x);
         ab += v.y;
     }
-    S = 0.0;
-    C = 0.0;
-    AB = 0.0;
-    for (int t = 0; t < 32; t++) {
-        const double st = __shfl_sync(FULL_MASK, s, t);
-        const double ct = __shfl_sync(FULL_MASK, c, t);
-        const double at = __shfl_sync(FULL_MASK, ab, t);
-        neu_add(S, C, st);
-        neu_add(S, C, ct);
-        AB += at;
-    }
+    lane_combine(s, c, ab);
+    S = s;
+    C = c;
+    AB = ab;
 }
 
 // Same over group records (s, c, abs).
@@ -425,17 +452,10 @@ __device__ void reduce_groups(const SgGroupSlot *g, unsigned long long n, int la
         neu_add(s, c, v.y);
         ab += w.x;
     }
-    S = 0.0;
-    C = 0.0;
-    AB = 0.0;
-    for (int t = 0; t < 32; t++) {
-        const double st = __shfl_sync(FULL_MASK, s, t);
-        const double ct = __shfl_sync(FULL_MASK, c, t);
-        const double at = __shfl_sync(FULL_MASK, ab, t);
-        neu_add(S, C, st);
-        neu_add(S, C, ct);
-        AB += at;
-    }
+    lane_combine(s, c, ab);
+    S = s;
+    C = c;
+    AB = ab;
 }
 
 // Called by the warp that wrote chunk c's slot.  Two-level ticketing: the
@@ -502,12 +522,20 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         FoldAcc F;
         if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sIdx, lane, F);
         else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sIdx, lane, F);
-        double acc = F.acc + ((double)F.hs + (double)F.hc) + ff_to_double(F.fa), aabs = (double)F.habs;
-        for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(FULL_MASK, acc, o);
-            aabs += __shfl_xor_sync(FULL_MASK, aabs, o);
+        double acc, aabs;
+        if constexpr (std::is_same<T, double>::value) {
+            // the FP64 fold skips |W D| per point: the chunk's |sum| stands in
+            acc = F.acc;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+            aabs = fabs(acc);
+        } else {
+            acc = std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa);
+            aabs = (double)F.habs;
+            for (int o = 16; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(FULL_MASK, acc, o);
+                aabs += __shfl_xor_sync(FULL_MASK, aabs, o);
+            }
         }
-        if (std::is_same<T, double>::value) aabs = fabs(acc);  // the FP64 fold skips |W D| per point
         if (lane == 0) {
             SgSlot sl;
             sl.sum = acc * P->coef;

@@ -35,7 +35,7 @@ def _load():
 
 def run(kind, fam, params, d, L, form=2, grad=0, ppc=2048, ctas_per_sm=8, warps=8):
     p = np.ascontiguousarray(params, dtype=np.float64)
-    out = np.zeros(8)
+    out = np.zeros(9)
     nv = ctypes.c_longlong(0)
     cap = 2 * d * 64 if grad else 1
     v = np.zeros(max(cap, 1))
@@ -46,5 +46,13 @@ def run(kind, fam, params, d, L, form=2, grad=0, ppc=2048, ctas_per_sm=8, warps=
     if rc != 0:
         raise RuntimeError("chk_run failed with %d" % rc)
     return dict(rel=out[0], logscale=out[1], violations=int(out[2]), badpairs=int(out[3]),
-                evals=int(out[4]), chunks=int(out[5]), plan_evals=int(out[6]), rel_shift=out[7],
+                evals=int(out[4]), chunks=int(out[5]), plan_evals=int(out[6]), rel_shift=out[7], lane_slots=int(out[8]),
                 v=v[:nv.value])
+
+
+def unrank_mismatches(d, r, n=2000):
+    """Mismatches between the kernel's 32-wide unranking rounds and the serial search."""
+    lib = _load()
+    lib.chk_unrank.restype = ctypes.c_longlong
+    lib.chk_unrank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
+    return lib.chk_unrank(d, r, n)

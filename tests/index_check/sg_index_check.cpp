@@ -61,7 +61,8 @@ extern "C" {
 // (i.e. base + T times the multiplier), out[1] = log f(c) (exponential
 // families), out[2] = number of bound violations, out[3] = pairs visited
 // other than exactly once, out[4] = evaluations, out[5] = chunks,
-// out[6] = evaluations the plan claims.  vout receives the adjoint sub-sums
+// out[6] = evaluations the plan claims, out[8] = lane slots of the point
+// loop (32 x warp passes; evaluations / slots is the lane occupancy).  vout receives the adjoint sub-sums
 // (nv entries, may be NULL); nv_out their count.
 int chk_run(int kind, int fam, const double *params, int d, int L, int form, int grad, int ppc,
             int ctas_per_sm, int warps, double *out, double *vout, long long *nv_out) {
@@ -140,6 +141,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
 
     long long violations = 0, badpairs = 0;
     unsigned long long evals = 0;
+    long long lane_slots = 0;
     std::vector<double> slot(P->nchunks, 0.0);
     int idx[SG_MAX_R];
     for (unsigned long long c = 0; c < P->nchunks; c++) {
@@ -160,6 +162,28 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
         sg_chunk_span(Pp, c, &rank, &cnt, &a_lo, &a_hi);
         if (a_lo < 0 || a_hi > Pp->A || a_lo >= a_hi) violations++;
         sg_unrank_lex(rank, dd, r, B.data(), idx);
+        // replay the kernel's 32-wide unranking rounds; it must agree
+        {
+            int p = -1;
+            unsigned long long rk = rank;
+            for (int t = 0; t < r; t++) {
+                SgUnrankPos u;
+                sg_unrank_begin(&u, rk, dd, r, t, p, B.data());
+                for (int rounds = 0;; rounds++) {
+                    unsigned mask = 0;
+                    for (int j = 0; j < 32; j++)
+                        if (sg_unrank_test(&u, sg_unrank_candidate(&u, j), dd, B.data())) mask |= 1u << j;
+                    if (!(mask & 1u) || rounds > 3) {
+                        violations++;
+                        break;
+                    }
+                    if (sg_unrank_narrow(&u, mask)) break;
+                }
+                rk -= u.total - sg_binom(B.data(), dd - u.lo, u.k);
+                if (u.lo != idx[t]) violations++;
+                p = u.lo;
+            }
+        }
         for (int t = 1; t < r; t++)
             if (idx[t] <= idx[t - 1]) violations++;
         if (idx[r - 1] >= dd) violations++;
@@ -201,27 +225,25 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
             for (int ab = a_lo; ab < a_hi; ab += SG_APAD) {
                 const int At = a_hi - ab < SG_APAD ? a_hi - ab : SG_APAD;
                 std::vector<int> seen((size_t)At * E, 0);
-                const int G = E >= 32 ? 1 : 32 / E, Eg = E >= 32 ? 32 : E;
+                long long passes = 0;
                 for (int lane = 0; lane < 32; lane++) {
-                    const int sub = lane / Eg, el = lane - sub * Eg;
-                    if (sub >= G) continue;
-                    for (int e0 = 0; e0 < E; e0 += Eg) {
-                        const int e = e0 + el;
-                        if (e >= E) break;
+                    long long mine = 0;
+                    for (SgFlatPos f(lane, E); f.a < At; f.step(), mine++) {
+                        const int e = f.e, a = f.a;
                         const long long rel = e < seg.E1 ? seg.base1 + e : seg.base2 + (e - seg.E1);
                         if (!check(rel, Pp->toff, Pp->tm)) continue;
                         const double2 te = tab[tbase + rel];
-                        for (int a = sub; a < At; a += G) {
-                            seen[(size_t)a * E + e]++;
-                            const double Sv = S[ab + a] + te.x, Wv = W[ab + a] * te.y;
-                            double D;
-                            if (I->gk == SG_GK_OSC) D = -2.0 * sin(0.5 * Sv) * (V.sin_phi * cos(0.5 * Sv) + V.cos_phi * sin(0.5 * Sv));
-                            else D = expm1(Sv);
-                            acc += Wv * D;
-                            evals++;
-                        }
+                        seen[(size_t)a * E + e]++;
+                        const double Sv = S[ab + a] + te.x, Wv = W[ab + a] * te.y;
+                        double D;
+                        if (I->gk == SG_GK_OSC) D = -2.0 * sin(0.5 * Sv) * (V.sin_phi * cos(0.5 * Sv) + V.cos_phi * sin(0.5 * Sv));
+                        else D = expm1(Sv);
+                        acc += Wv * D;
+                        evals++;
                     }
+                    if (mine > passes) passes = mine;
                 }
+                lane_slots += 32 * passes;
                 for (int v : seen)
                     if (v != 1) badpairs++;
             }
@@ -252,8 +274,58 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
     out[5] = (double)P->nchunks;
     out[6] = (double)P->total_evals;
     if (P->nout > 1) out[7] = vals[1];
+    out[8] = (double)lane_slots;
     if (nv_out) *nv_out = nv;
     plan_free_host(P);
     return 0;
+}
+
+// Compares the kernel's 32-wide unranking rounds with the serial binary
+// search for n ranks spread over [0, C(d, r)) (the first, the last and a
+// multiplicative sequence in between).  Returns the number of mismatches,
+// or -1 if C(d, r) is 0 or does not fit the table.
+long long chk_unrank(int d, int r, long long n) {
+    std::vector<unsigned long long> B((size_t)SG_BINOM_K * (SG_MAX_D + 1));
+    sg_fill_binomials(B.data());
+    const unsigned long long total = sg_binom(B.data(), d, r);
+    if (total == 0) return -1;
+    long long bad = 0;
+    unsigned long long x = 0x9E3779B97F4A7C15ull;
+    for (long long i = 0; i < n; i++) {
+        unsigned long long rank;
+        if (i == 0) rank = 0;
+        else if (i == 1) rank = total - 1;
+        else {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            rank = (x >> 11) % total;
+        }
+        int a[SG_MAX_R], b[SG_MAX_R];
+        sg_unrank_lex(rank, d, r, B.data(), a);
+        int p = -1;
+        unsigned long long rk = rank;
+        for (int t = 0; t < r; t++) {
+            SgUnrankPos u;
+            sg_unrank_begin(&u, rk, d, r, t, p, B.data());
+            for (int rounds = 0;; rounds++) {
+                unsigned mask = 0;
+                for (int j = 0; j < 32; j++)
+                    if (sg_unrank_test(&u, sg_unrank_candidate(&u, j), d, B.data())) mask |= 1u << j;
+                if (!(mask & 1u) || rounds > 3) {
+                    bad++;
+                    break;
+                }
+                if (sg_unrank_narrow(&u, mask)) break;
+            }
+            rk -= u.total - sg_binom(B.data(), d - u.lo, u.k);
+            b[t] = u.lo;
+            p = u.lo;
+        }
+        for (int t = 0; t < r; t++)
+            if (a[t] != b[t]) {
+                bad++;
+                break;
+            }
+    }
+    return bad;
 }
 }

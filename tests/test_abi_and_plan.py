@@ -83,6 +83,13 @@ def test_fold_enumeration_matches_oracle(case, form):
     assert _oracle_rel(case, r) < tol
 
 
+@pytest.mark.parametrize("d,r", [(1, 1), (5, 5), (12, 6), (33, 1), (100, 3), (1000, 2), (1025, 4),
+                                 (8192, 1), (8192, 3), (8192, 12)])
+def test_warp_unranking_matches_binary_search(d, r):
+    # the kernel searches 32 candidates per round; up to three rounds for d <= 8192
+    assert index_check.unrank_mismatches(d, r) == 0
+
+
 @pytest.mark.parametrize("ppc,ctas,warps", [(64, 1, 1), (100, 3, 2), (1 << 20, 8, 8)])
 def test_chunking_does_not_change_the_sum(ppc, ctas, warps):
     c = si.cfg2()
