@@ -165,14 +165,15 @@ SG_HD void sg_chunk_span(const SgPatDev *P, unsigned long long c, unsigned long 
                          unsigned long long *cnt, int *a_lo, int *a_hi) {
     const unsigned long long local = c - P->chunk0;
     if (P->asplit <= 1) {
-        *rank = local * P->spc;
+        *rank = P->rank0 + local * P->spc;
         *cnt = P->nsub - *rank < P->spc ? P->nsub - *rank : P->spc;
         *a_lo = 0;
         *a_hi = P->A;
     } else {
-        *rank = local / (unsigned long long)P->asplit;
+        const unsigned long long sub = local / (unsigned long long)P->asplit;
+        *rank = P->rank0 + sub;
         *cnt = 1;
-        const int blk = (int)(local - *rank * (unsigned long long)P->asplit);
+        const int blk = (int)(local - sub * (unsigned long long)P->asplit);
         *a_lo = blk * P->ablk;
         *a_hi = *a_lo + P->ablk < P->A ? *a_lo + P->ablk : P->A;
     }

@@ -67,7 +67,9 @@ struct SgItemVar {
     double sin_phi, cos_phi;    // oscillatory phase of the per-point deviation
 };
 
-// One pattern of one item.
+// One pattern of one item, or a contiguous range of its subsets (the planner
+// may give the end of the work queue smaller chunks, and then splits a
+// pattern into two records).
 struct SgPatDev {
     int item;         // index into the item array
     int r;            // active directions (prefix r-1, tail 1)
@@ -77,7 +79,8 @@ struct SgPatDev {
     long long poff[SG_MAX_R - 1];  // table offsets of the prefix blocks
     int pm[SG_MAX_R - 1];          // nodes per direction of the prefix blocks
     double coef;      // multiplier of the pattern's sum (1, or Eq. 2.6 coefficient)
-    unsigned long long nsub;   // C(d, r) subsets
+    unsigned long long rank0;  // first subset rank of this record
+    unsigned long long nsub;   // end rank (exclusive): subsets [rank0, nsub) of the C(d, r)
     unsigned long long spc;    // subsets per chunk (1 when a subset is split)
     int asplit;                // chunks per subset (prefix-tuple blocks); 1 = no split
     int ablk;                  // prefix tuples per block when split
@@ -105,9 +108,13 @@ struct SgOutDev {
     double mant, exp2, value, cond, err_est, sum, abs_sum;
 };
 
-// Base quantities of an integral: Q = scale * (base + T), scale = exp(log_hi + log_lo).
+// Base quantities of an integral: Q = scale * (base + T), scale = exp(log_hi + log_lo)
+// = 2^scale_e2 * scale_m (split once by the setup kernel, so that assembling
+// a finished item needs no exponential).
 struct SgBaseDev {
     double log_hi, log_lo;   // log of f(c) (exponential kinds), 0 for oscillatory
     double base;             // 1 or cos(theta_c)
     double sin_th, cos_th;   // theta_c for the oscillatory kind
+    double scale_e2;         // integer power of two of the scale
+    double scale_m;          // the scale's remaining factor, in [2^-1/2, 2^1/2]
 };

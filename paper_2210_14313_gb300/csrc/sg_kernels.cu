@@ -373,12 +373,10 @@ __device__ void assemble_item(const SgItemDev *items, const SgItemVar *vars, con
         return;
     }
     const SgBaseDev B = bases[g];
-    // Q = exp(log_hi + log_lo) * rel = 2^e0 * exp(r) * rel, ln 2 split in two (Cody & Waite)
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double e0 = floor(B.log_hi * 1.44269504088896338700);
-    const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
+    // Q = exp(log_hi + log_lo) * rel = 2^e0 * scale_m * rel
+    const double e0 = B.scale_e2;
     int e1 = 0;
-    const double mant = frexp(exp(rr) * rel, &e1);
+    const double mant = frexp(B.scale_m * rel, &e1);
     SgOutDev o;
     o.mant = mant;
     o.exp2 = e0 + e1;
@@ -398,63 +396,81 @@ __device__ void assemble_item(const SgItemDev *items, const SgItemVar *vars, con
 // lane ends with the same result; the tree is fixed, so the result does not
 // depend on which warp runs it.  Five levels of dependent FP64 work instead
 // of a 32-step lane-serial sum.
+// (s, c) += (s2, c2) for compensated pairs; symmetric in its two operands.
+__device__ __forceinline__ void pair_add(double &s, double &c, double s2, double c2) {
+    const double t = __dadd_rn(s, s2);
+    const double z = __dsub_rn(t, s);
+    const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(s2, z));
+    s = t;
+    c = __dadd_rn(__dadd_rn(c, c2), e);
+}
+
 __device__ __forceinline__ void lane_combine(double &s, double &c, double &ab) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const double s2 = __shfl_xor_sync(FULL_MASK, s, o);
         const double c2 = __shfl_xor_sync(FULL_MASK, c, o);
         const double a2 = __shfl_xor_sync(FULL_MASK, ab, o);
-        const double t = __dadd_rn(s, s2);
-        const double z = __dsub_rn(t, s);
-        const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(s2, z));
-        s = t;
-        c = __dadd_rn(__dadd_rn(c, c2), e);
+        pair_add(s, c, s2, c2);
         ab = __dadd_rn(ab, a2);
     }
 }
 
-// Lane l adds x[l], x[l+32], ... (Neumaier), then the lanes are combined by
-// lane_combine: a fixed summation order whichever warp runs it.  Eight loads
-// are in flight per lane so that the L2 latency overlaps.
+// Lane l adds x[l], x[l+32], ... into four compensated accumulators (the
+// t-th load of a batch into accumulator t mod 4, four independent chains),
+// which are then merged and the lanes combined by lane_combine: a fixed
+// summation order whichever warp runs it.  Each lane issues its loads eight
+// at a time (missing ones read as zero, which leaves a compensated sum
+// unchanged), so that the L2 latency is paid once per batch.
 __device__ void reduce_slots(const double2 *slots, unsigned long long n, int lane, double &S,
                              double &C, double &AB) {
-    double s = 0.0, c = 0.0, ab = 0.0;
-    unsigned long long q = lane;
-    for (; q + 7 * 32 < n; q += 8 * 32) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0}, ab = 0.0;
+    for (unsigned long long q0 = lane; q0 < n; q0 += 8 * 32) {
         double2 v[8];
 #pragma unroll
-        for (int t = 0; t < 8; t++) v[t] = __ldcg(slots + q + t * 32);
+        for (int t = 0; t < 8; t++) {
+            const unsigned long long q = q0 + t * 32;
+            v[t] = q < n ? __ldcg(slots + q) : make_double2(0.0, 0.0);
+        }
 #pragma unroll
         for (int t = 0; t < 8; t++) {
-            neu_add(s, c, v[t].x);
+            neu_add(s[t & 3], c[t & 3], v[t].x);
             ab += v[t].y;
         }
     }
-    for (; q < n; q += 32) {
-        const double2 v = __ldcg(slots + q);
-        neu_add(s, c, v.x);
-        ab += v.y;
-    }
-    lane_combine(s, c, ab);
-    S = s;
-    C = c;
+    pair_add(s[0], c[0], s[1], c[1]);
+    pair_add(s[2], c[2], s[3], c[3]);
+    pair_add(s[0], c[0], s[2], c[2]);
+    lane_combine(s[0], c[0], ab);
+    S = s[0];
+    C = c[0];
     AB = ab;
 }
 
 // Same over group records (s, c, abs).
 __device__ void reduce_groups(const SgGroupSlot *g, unsigned long long n, int lane, double &S,
                               double &C, double &AB) {
-    double s = 0.0, c = 0.0, ab = 0.0;
-    for (unsigned long long q = lane; q < n; q += 32) {
-        const double2 v = __ldcg((const double2 *)(g + q));
-        const double2 w = __ldcg((const double2 *)(g + q) + 1);
-        neu_add(s, c, v.x);
-        neu_add(s, c, v.y);
-        ab += w.x;
+    double s[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0}, ab = 0.0;
+    for (unsigned long long q0 = lane; q0 < n; q0 += 8 * 32) {
+        double2 v[8], w[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const unsigned long long q = q0 + t * 32;
+            v[t] = q < n ? __ldcg((const double2 *)(g + q)) : make_double2(0.0, 0.0);
+            w[t] = q < n ? __ldcg((const double2 *)(g + q) + 1) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            pair_add(s[t & 3], c[t & 3], v[t].x, v[t].y);
+            ab += w[t].x;
+        }
     }
-    lane_combine(s, c, ab);
-    S = s;
-    C = c;
+    pair_add(s[0], c[0], s[1], c[1]);
+    pair_add(s[2], c[2], s[3], c[3]);
+    pair_add(s[0], c[0], s[2], c[2]);
+    lane_combine(s[0], c[0], ab);
+    S = s[0];
+    C = c[0];
     AB = ab;
 }
 
@@ -628,6 +644,15 @@ __global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
             B.base = 1.0;
             B.sin_th = 0.0;
             B.cos_th = 1.0;
+        }
+        // exp(log_hi + log_lo) = 2^e0 exp(r), r = log_hi - e0 ln 2 + log_lo with ln 2
+        // split in two (Cody & Waite): the result's scale without overflow
+        {
+            const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+            const double e0 = floor(B.log_hi * 1.44269504088896338700);
+            const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
+            B.scale_e2 = e0;
+            B.scale_m = exp(rr);
         }
         if (lane == 0) A.bases[g] = B;
         if (!A.do_items) return;

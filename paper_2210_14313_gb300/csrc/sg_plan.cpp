@@ -256,13 +256,25 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     // the per-chunk work (unranking, prefix folds, one slot) dominates, never
     // above the tuned maximum, and at most 2^24 chunk slots
     const u64 warps = (u64)std::max<long long>(resident_warps, 1);
-    const u64 floor_evals = prec ? 2048 : 32;
-    const u64 per_warp = prec ? 4 : 8;  // FP64 chunks are costly: more of them even the tail out
+    // chunks per resident warp and the smallest chunk: a chunk's fixed work
+    // (grab, unranking, prefix folds, reduction) costs about 15k warp
+    // cycles, so chunks are a few per warp; the guided tail below evens out
+    // the end of the queue.  Values from sweeps on GB300 (cfg2/cfg3 FP64,
+    // cfg3 float, cfg2/cfg5 float-float).
+    const u64 floor_evals = prec == 0 ? 32 : 1024;
+    const u64 per_warp = prec == 1 ? 4 : 2;
     u64 target = total / (per_warp * warps) + 1;
     if (target < floor_evals) target = floor_evals;
     if (target > (u64)tune.points_per_chunk) target = (u64)tune.points_per_chunk;
     const u64 max_chunks = 1ull << 24;
     if (total / target > max_chunks) target = total / max_chunks + 1;
+    // guided tail: the last eighth of the queue gets chunks of a quarter of
+    // the size, so that the warps drain it together instead of waiting for
+    // a few full-size chunks grabbed last
+    const u64 tail_cut = total - total / 8;
+    u64 tail_target = std::max<u64>(target / 4, 16);
+    if (total / tail_target > max_chunks) tail_target = target;
+    u64 done = 0;
     u64 chunk = 0;
     for (size_t q = 0; q < order.size(); q++) {
         ItemBuild &b = ib[order[q]];
@@ -288,23 +300,45 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
             pd.toff = relmap[g].at(sp.tail);
             pd.coef = sp.coef;
             const u64 per_sub = A * (u64)pd.tm;
-            pd.chunk0 = chunk;
-            if (per_sub > target && A > 1) {
-                // split each subset's prefix tuples over several chunks
-                u64 parts = (per_sub + target - 1) / target;
-                if (parts > A) parts = A;
-                pd.ablk = (int)((A + parts - 1) / parts);
-                pd.asplit = (int)((A + pd.ablk - 1) / pd.ablk);
-                pd.spc = 1;
-                chunk += pd.nsub * (u64)pd.asplit;
+            const u64 nsub = pd.nsub;
+            // one record for subsets [r0, r1) with chunk target tgt
+            auto emit = [&](u64 r0, u64 r1, u64 tgt) {
+                SgPatDev rec = pd;
+                rec.rank0 = r0;
+                rec.nsub = r1;
+                rec.chunk0 = chunk;
+                if (per_sub > tgt && A > 1) {
+                    // split each subset's prefix tuples over several chunks
+                    u64 parts = (per_sub + tgt - 1) / tgt;
+                    if (parts > A) parts = A;
+                    rec.ablk = (int)((A + parts - 1) / parts);
+                    rec.asplit = (int)((A + rec.ablk - 1) / rec.ablk);
+                    rec.spc = 1;
+                    chunk += (r1 - r0) * (u64)rec.asplit;
+                } else {
+                    rec.asplit = 1;
+                    rec.ablk = (int)A;
+                    rec.spc = std::max<u64>(1, tgt / per_sub);
+                    chunk += (r1 - r0 + rec.spc - 1) / rec.spc;
+                }
+                P->pats.push_back(rec);
+                P->pat_chunk0.push_back(rec.chunk0);
+            };
+            const u64 pe = nsub * per_sub;
+            if (done >= tail_cut || tail_target == target) {
+                emit(0, nsub, done >= tail_cut ? tail_target : target);
+            } else if (done + pe > tail_cut) {
+                const u64 head = (tail_cut - done + per_sub - 1) / per_sub;  // subsets before the cut
+                if (head >= nsub) {
+                    emit(0, nsub, target);
+                } else {
+                    emit(0, head, target);
+                    emit(head, nsub, tail_target);
+                }
             } else {
-                pd.asplit = 1;
-                pd.ablk = (int)A;
-                pd.spc = std::max<u64>(1, target / per_sub);
-                chunk += (pd.nsub + pd.spc - 1) / pd.spc;
+                emit(0, nsub, target);
             }
-            P->pats.push_back(pd);
-            P->pat_chunk0.push_back(pd.chunk0);
+            done += pe;
         }
         b.it.npat = (int)((long long)P->pats.size() - b.it.pat0);
         b.it.nchunk = chunk - b.it.chunk0;
