@@ -122,6 +122,65 @@ __device__ __forceinline__ float sg_expm1f(float x) {
     return fmaf(scale, p, scale - 1.0f);
 }
 
+// sin and cos in double for the fold (|x| < 2^20; larger arguments, Inf and
+// NaN take CUDA's sincos out of line).  Cody & Waite reduction
+// x = k pi/2 + r with pi/2 in three parts, the first two of 33 significant
+// bits so that k * part is exact for |k| < 2^20; k is rounded by adding
+// 1.5 * 2^52 to x * 2/pi, whose low word then holds k mod 2^32 (the
+// quadrant).  On |r| <= pi/4 (plus rounding) the Taylor series of sin to
+// r^15 and of cos to r^16 leave truncation errors below 7e-17 relative and
+// 3e-18 absolute.  The quadrant swaps and sign flips are integer operations
+// on the result words, so the function costs 22 FP64 instructions.
+__device__ __noinline__ double2 sg_sincos_slow(double x) {
+    double s, c;
+    sincos(x, &s, &c);
+    return make_double2(s, c);
+}
+
+__device__ __forceinline__ double sg_flip_sign(double v, unsigned m) {
+    return __hiloint2double(__double2hiint(v) ^ (int)m, __double2loint(v));
+}
+
+__device__ __forceinline__ void sg_sincos_d(double x, double *sp, double *cp) {
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x41300000) {  // |x| >= 2^20, Inf, NaN
+        const double2 v = sg_sincos_slow(x);
+        *sp = v.x;
+        *cp = v.y;
+        return;
+    }
+    const double magic = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, 6.36619772367581382433e-01, magic);
+    const unsigned q = (unsigned)__double2loint(t);
+    const double k = t - magic;
+    double r = fma(-k, 1.57079632673412561417e+00, x);  // pi/2 head (33 bits)
+    r = fma(-k, 6.07710050630396597660e-11, r);          // middle (33 bits)
+    r = fma(-k, 2.02226624879595063540e-21, r);          // tail
+    const double z = r * r;
+    // sin r = r + r z (-1/3! + z (1/5! - z (1/7! - ... - z/15!)))
+    double ps = -7.64716373181981647590e-13;          // -1/15!
+    ps = fma(ps, z, 1.60590438368216145994e-10);      //  1/13!
+    ps = fma(ps, z, -2.50521083854417187751e-08);     // -1/11!
+    ps = fma(ps, z, 2.75573192239858906526e-06);      //  1/9!
+    ps = fma(ps, z, -1.98412698412698412526e-04);     // -1/7!
+    ps = fma(ps, z, 8.33333333333333321769e-03);      //  1/5!
+    ps = fma(ps, z, -1.66666666666666657415e-01);     // -1/3!
+    const double sr = fma(r * z, ps, r);
+    // cos r = 1 + z (-1/2! + z (1/4! - z (1/6! - ... + z/16!)))
+    double pc = 4.77947733238738529744e-14;           //  1/16!
+    pc = fma(pc, z, -1.14707455977297247139e-11);     // -1/14!
+    pc = fma(pc, z, 2.08767569878680989792e-09);      //  1/12!
+    pc = fma(pc, z, -2.75573192239858906526e-07);     // -1/10!
+    pc = fma(pc, z, 2.48015873015873015873e-05);      //  1/8!
+    pc = fma(pc, z, -1.38888888888888894189e-03);     // -1/6!
+    pc = fma(pc, z, 4.16666666666666643537e-02);      //  1/4!
+    pc = fma(pc, z, -0.5);                            // -1/2!
+    const double cr = fma(z, pc, 1.0);
+    // x = k pi/2 + r: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s) for k mod 4
+    const double a = (q & 1u) ? cr : sr, b = (q & 1u) ? sr : cr;
+    *sp = sg_flip_sign(a, (q & 2u) << 30);
+    *cp = sg_flip_sign(b, ((q + 1u) & 2u) << 30);
+}
+
 // Per-point deviation (the "G" evaluation).
 template <typename T, int GK> __device__ __forceinline__ T gdev(T S, T sphi, T cphi);
 template <> __device__ __forceinline__ float gdev<float, SG_GK_EXPM1>(float S, float, float) {
@@ -140,7 +199,7 @@ template <> __device__ __forceinline__ float gdev<float, SG_GK_OSC>(float H, flo
 }
 template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double H, double sphi, double cphi) {
     double sh, ch;
-    sincos(H, &sh, &ch);
+    sg_sincos_d(H, &sh, &ch);
     return sh * fma(sphi, ch, cphi * sh);
 }
 
@@ -994,7 +1053,7 @@ __global__ void sg_fn_kernel(int kind, int prec, const double *x, double *y, int
             y[2 * i + 1] = c;
         } else {
             double s, c;
-            sincos(x[i], &s, &c);
+            sg_sincos_d(x[i], &s, &c);
             y[2 * i] = s;
             y[2 * i + 1] = c;
         }

@@ -1,6 +1,6 @@
 """Accuracy of the elementary functions the fold evaluates per point (the
-library's own float expm1; CUDA's sincosf / sincos for the oscillatory
-deviation) on the GPU against numpy's double-precision libm, through the
+library's own float expm1 and double sincos; CUDA's sincosf for the
+oscillatory deviation in float) on the GPU against numpy's double-precision libm, through the
 sg_eval_functions hook of the C ABI."""
 import ctypes
 
@@ -59,7 +59,10 @@ def test_float_sincos_accuracy():
 
 
 def test_double_sincos_accuracy():
-    x = _args(-60.0, 60.0)
+    # the fold's own double sincos (Cody-Waite reduction, Taylor series) and,
+    # from |x| = 2^20 on, the library sincos it defers to
+    x = np.concatenate([_args(-60.0, 60.0), np.arange(-40, 41) * (0.5 * np.pi),
+                        [1048575.75, 1048576.0, -1048576.5, 3.0e7, -1.0e10, 123456789.125]])
     y = _eval(1, sg.PREC_FP64, x)
     s, c = y[0::2], y[1::2]
     rs, rc = np.sin(x), np.cos(x)
