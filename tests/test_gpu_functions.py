@@ -1,6 +1,6 @@
 """Accuracy of the elementary functions the fold evaluates per point (the
-library's own float expm1 and double sincos; CUDA's sincosf for the
-oscillatory deviation in float) on the GPU against numpy's double-precision libm, through the
+library's own float expm1, double expm1 and double sincos; CUDA's sincosf
+for the oscillatory deviation in float) on the GPU against numpy's double-precision libm, through the
 sg_eval_functions hook of the C ABI."""
 import ctypes
 
@@ -70,6 +70,20 @@ def test_double_sincos_accuracy():
     assert np.abs(c - rc).max() <= 4 * U64
     small = (np.abs(x) < 0.5) & (x != 0)
     assert (np.abs(s - rs)[small] / np.abs(rs[small])).max() <= 2 * U64
+
+
+def test_double_expm1_accuracy():
+    # the fold's own double expm1: short series below 2^-5, long series below
+    # ln2/2, reduction above, the library expm1 from |x| = 700 on
+    x = np.concatenate([_args(-40.0, 40.0), _args(-0.4, 0.4, n=50001), _args(-0.04, 0.04, n=50001),
+                        [2.0 ** -5, -2.0 ** -5, 0.3465733528137207, -0.3465733528137207, 699.0, -699.0,
+                         700.0, -745.0, 709.5]])
+    y = _eval(0, sg.PREC_FP64, x)
+    ref = np.expm1(x)
+    ok = np.isfinite(ref) & (ref != 0)
+    rel = np.abs(y[ok] - ref[ok]) / np.abs(ref[ok])
+    assert rel.max() <= 3 * U64, (rel.max(), x[ok][rel.argmax()])
+    assert y[x == 0.0].tolist() == [0.0] * int((x == 0.0).sum())
 
 
 def test_float_float_expm1():
