@@ -15,17 +15,20 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sg_oracle.c")
+_DEPS = [_SRC, os.path.join(_HERE, "sg_gp_table.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 FORM_DIFF = 0
 FORM_COMB = 1
+GP = 3     # Gauss-Patterson (rule kinds 1, 2, 4 as in the library)
+SLOW = 16  # flag OR'ed into a rule kind: the paper's delayed growth (Section 5.4)
 
 
 def build(force: bool = False) -> str:
     """Compile sg_oracle.c into liboracle.so next to it (gcc, IEEE double,
     no FMA contraction so that x86 and Arm hosts round identically)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(p) for p in _DEPS):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC",
                                "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
@@ -52,6 +55,8 @@ def _load():
         lib.or_points.restype = ctypes.c_long
         lib.or_count_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.or_count_points.restype = ctypes.c_uint64
+        lib.or_count_distinct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.or_count_distinct.restype = ctypes.c_uint64
         lib.or_gradient.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ip,
                                     ctypes.c_int, ctypes.c_int, dp, dp]
         lib.or_gradient.restype = ctypes.c_int
@@ -144,3 +149,8 @@ def points(kind: int, d: int, L: int, form: int = FORM_DIFF):
 def count_points(kind: int, d: int, L: int) -> int:
     """n_d^q: point count of Eq. 2.6's tensor grids, with repetition."""
     return int(_load().or_count_points(kind, d, L))
+
+
+def count_distinct(kind: int, d: int, L: int) -> int:
+    """Distinct points of the sparse grid of a nested rule (0 for Gauss-Legendre)."""
+    return int(_load().or_count_distinct(kind, d, L))

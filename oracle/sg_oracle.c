@@ -29,7 +29,17 @@
  * w -> w/2):
  *   trapezoid        Eq. 2.10; level 1 read as the single midpoint, weight 1
  *   Clenshaw-Curtis  Eq. 2.11; n_1 = 1, n_l = 2^(l-1) + 1, explicit weights
+ *   Gauss-Patterson  Eq. 2.12; n_l = 2^l - 1, nested; nodes and weights from
+ *                    the table sg_gp_table.h (Patterson extensions computed
+ *                    at 300 digits by gen_gp_table.py)
  *   Gauss-Legendre   Eq. 2.13; n_l = l, zeros of P_l by Newton's method
+ * Growth: by default level l is the rule's l-th member.  With the flag
+ * OR_SLOW in `kind`, level l is the smallest member exact for polynomials of
+ * degree 2l - 1 (the paper's accuracy-level convention of Section 5.4:
+ * trapezoid and Clenshaw-Curtis N = 1, 3, 5, 9, 9, 17, 17, 17, 17, 33, ...;
+ * Gauss-Patterson N = 1, 3, 3, 7, 7, 7, 15, ...); Gauss-Legendre has n_l = l
+ * either way.  Two consecutive levels on the same member have a zero
+ * difference rule.
  *
  * Parameters: params[0..d) = a, params[d..2d) = u, for every family:
  *   0 exp-linear   f = exp(sum a_i x_i)
@@ -53,9 +63,13 @@
 #include <string.h>
 #include <unistd.h>
 
-#define OR_MAX_LEVEL 13 /* 4097 nodes at most per 1-D rule */
+#include "sg_gp_table.h"
 
-enum { R_TRAP = 1, R_CC = 2, R_GL = 4 };
+#define OR_MAX_LEVEL 13 /* largest member of a nested rule: 4097 nodes */
+#define OR_MAX_ACC 32   /* largest accuracy level (levels 1 .. L + 1) */
+#define OR_SLOW 16      /* flag in `kind`: the paper's delayed growth */
+
+enum { R_TRAP = 1, R_CC = 2, R_GP = 3, R_GL = 4 };
 enum { F_EXPLIN = 0, F_OSC = 1, F_PEAK = 2, F_GAUSS = 3, F_GAUSSLIN = 4 };
 enum { FORM_DIFF = 0, FORM_COMB = 1 };
 
@@ -63,11 +77,39 @@ enum { FORM_DIFF = 0, FORM_COMB = 1 };
 /* 1-D rules                                                                 */
 /* ------------------------------------------------------------------------ */
 
-static int level_nodes(int kind, int level) {
+/* Node count of member r of a rule family (0 if out of range). */
+static int member_nodes(int rule, int r) {
+    if (r < 1) return 0;
+    if (rule == R_GL) return r <= OR_MAX_LEVEL ? r : 0;
+    if (rule == R_GP) return r <= OR_GP_LEVELS ? (1 << r) - 1 : 0;
+    if (rule != R_CC && rule != R_TRAP) return 0;
+    if (r > OR_MAX_LEVEL) return 0;
+    return r == 1 ? 1 : (1 << (r - 1)) + 1;
+}
+
+/* Degree of polynomial exactness that selects member r under the delayed
+ * growth: Clenshaw-Curtis with n (odd) nodes integrates degree n exactly (the
+ * trapezoid rule follows the same sequence, Section 5.4); Gauss-Patterson
+ * with 2^r - 1 nodes is exact to degree 3 * 2^(r-1) - 1 (degree 1 for r = 1). */
+static int member_degree(int rule, int r) {
+    if (rule == R_GP) return r == 1 ? 1 : 3 * (1 << (r - 1)) - 1;
+    return member_nodes(R_CC, r);
+}
+
+/* Member of the rule family that serves accuracy level `level`. */
+static int level_member(int kind, int level) {
+    int rule = kind & 15;
     if (level < 1) return 0;
-    if (kind == R_GL) return level;
-    if (level == 1) return 1;
-    return (1 << (level - 1)) + 1;
+    if (!(kind & OR_SLOW) || rule == R_GL) return level;
+    for (int r = 1; r <= OR_MAX_LEVEL; r++) {
+        if (member_nodes(rule, r) == 0) return 0;
+        if (member_degree(rule, r) >= 2 * level - 1) return r;
+    }
+    return 0;
+}
+
+static int level_nodes(int kind, int level) {
+    return member_nodes(kind & 15, level_member(kind, level));
 }
 
 /* Legendre P_n and P_{n-1} at x by the three-term recurrence. */
@@ -154,11 +196,18 @@ static void trap_rule(int n, double *x, double *w) {
 /* Level-l rule on [0,1], nodes ascending.  Returns the node count. */
 int or_rule(int kind, int level, double *x, double *w) {
     int n = level_nodes(kind, level);
-    if (n <= 0 || level > OR_MAX_LEVEL) return -1;
+    int rule = kind & 15;
+    if (n <= 0 || (kind & ~(15 | OR_SLOW))) return -1;
     if (!x || !w) return n;
-    if (kind == R_GL) gl_rule(n, x, w);
-    else if (kind == R_CC) cc_rule(n, x, w);
-    else if (kind == R_TRAP) trap_rule(n, x, w);
+    if (rule == R_GP) {  /* tabulated on [0,1] already */
+        int r = level_member(kind, level);
+        memcpy(x, or_gp_x[r], sizeof(double) * n);
+        memcpy(w, or_gp_w[r], sizeof(double) * n);
+        return n;
+    }
+    if (rule == R_GL) gl_rule(n, x, w);
+    else if (rule == R_CC) cc_rule(n, x, w);
+    else if (rule == R_TRAP) trap_rule(n, x, w);
     else return -1;
     for (int j = 0; j < n; j++) {
         x[j] = 0.5 * (x[j] + 1.0);
@@ -174,20 +223,25 @@ int or_rule(int kind, int level, double *x, double *w) {
  * no node, so the union is the concatenation.  Returns the node count. */
 int or_delta_rule(int kind, int level, double *x, double *w) {
     int n = level_nodes(kind, level);
-    if (n <= 0 || level > OR_MAX_LEVEL) return -1;
+    int rule = kind & 15;
+    if (n <= 0 || (kind & ~(15 | OR_SLOW))) return -1;
     if (level == 1) return or_rule(kind, 1, x, w);
+    /* same member as the level below: the difference rule is zero */
+    if (level_member(kind, level) == level_member(kind, level - 1)) return 0;
     int n0 = level_nodes(kind, level - 1);
-    int nested = (kind != R_GL);
+    int nested = (rule != R_GL);
     int total = nested ? n : n + n0;
     if (!x || !w) return total;
-    double x0[1 << OR_MAX_LEVEL], w0[1 << OR_MAX_LEVEL];
+    double x0[(1 << (OR_MAX_LEVEL - 1)) + 1], w0[(1 << (OR_MAX_LEVEL - 1)) + 1];
     or_rule(kind, level, x, w);
     or_rule(kind, level - 1, x0, w0);
     if (nested) {
-        if (level == 2) {
+        /* node j of the coarser member is node 2j (trapezoid, CC: shared
+         * ends) or 2j + 1 (Gauss-Patterson: a new node in every gap) */
+        if (n0 == 1) {
             w[n / 2] -= w0[0];
         } else {
-            for (int j = 0; j < n0; j++) w[2 * j] -= w0[j];
+            for (int j = 0; j < n0; j++) w[2 * j + (rule == R_GP)] -= w0[j];
         }
     } else {
         for (int j = 0; j < n0; j++) {
@@ -337,10 +391,10 @@ static double family_val(const family *F, const double *x) {
  * is both Delta_1 and J^1. */
 typedef struct {
     int kind, d, L, form;
-    int n[OR_MAX_LEVEL + 1];
-    double *x[OR_MAX_LEVEL + 1], *w[OR_MAX_LEVEL + 1];
+    int n[OR_MAX_ACC + 1];
+    double *x[OR_MAX_ACC + 1], *w[OR_MAX_ACC + 1];
     int K_lo;                     /* lowest |k| that belongs to the rule */
-    double coef[OR_MAX_LEVEL + 1]; /* multiplier per |k| */
+    double coef[OR_MAX_ACC + 1]; /* multiplier per |k| */
 } grid;
 
 static double binom(int n, int k) {
@@ -352,8 +406,9 @@ static double binom(int n, int k) {
 
 static int grid_init(grid *G, int kind, int d, int L, int form) {
     memset(G, 0, sizeof(*G));
-    if (d < 1 || L < 0 || L + 1 > OR_MAX_LEVEL) return -1;
-    if (kind != R_TRAP && kind != R_CC && kind != R_GL) return -1;
+    if (d < 1 || L < 0 || L + 1 > OR_MAX_ACC) return -1;
+    for (int l = 1; l <= L + 1; l++)
+        if (or_rule(kind, l, 0, 0) <= 0) return -1;
     G->kind = kind; G->d = d; G->L = L; G->form = form;
     for (int k = 1; k <= L; k++) {
         int n = (form == FORM_DIFF) ? or_delta_rule(kind, k + 1, 0, 0) : or_rule(kind, k + 1, 0, 0);
@@ -575,8 +630,10 @@ long or_points(int kind, int d, int L, int form, double *X, double *W, long cap)
  * count with repetition), summed dimension by dimension as a polynomial in
  * the excess.  Exact below 2^64. */
 uint64_t or_count_points(int kind, int d, int L) {
-    if (d < 1 || L < 0 || L + 1 > OR_MAX_LEVEL) return 0;
-    unsigned __int128 c[OR_MAX_LEVEL + 1] = {0}, nc[OR_MAX_LEVEL + 1];
+    if (d < 1 || L < 0 || L + 1 > OR_MAX_ACC) return 0;
+    for (int l = 1; l <= L + 1; l++)
+        if (or_rule(kind, l, 0, 0) <= 0) return 0;
+    unsigned __int128 c[OR_MAX_ACC + 1] = {0}, nc[OR_MAX_ACC + 1];
     c[0] = 1;
     for (int i = 0; i < d; i++) {
         for (int K = 0; K <= L; K++) nc[K] = 0;
@@ -588,6 +645,31 @@ uint64_t or_count_points(int kind, int d, int L) {
     unsigned __int128 tot = 0;
     int lo = L - d + 1 > 0 ? L - d + 1 : 0;
     for (int K = lo; K <= L; K++) tot += c[K];
+    return (uint64_t)tot;
+}
+
+/* Distinct points of the sparse grid of a nested rule (trapezoid,
+ * Clenshaw-Curtis, Gauss-Patterson).  In one dimension the points new at
+ * level l are n_l - n_{l-1} (n_0 = 0); a point of the grid belongs to exactly
+ * one multi-index l with |l| <= q at which each of its coordinates is new, so
+ * the count is sum_{|l| <= q} prod_i (n_{l_i} - n_{l_i - 1}).  0 for
+ * Gauss-Legendre (not nested) or invalid arguments.  Exact below 2^64. */
+uint64_t or_count_distinct(int kind, int d, int L) {
+    if ((kind & 15) == R_GL) return 0;
+    if (d < 1 || L < 0 || L + 1 > OR_MAX_ACC) return 0;
+    for (int l = 1; l <= L + 1; l++)
+        if (or_rule(kind, l, 0, 0) <= 0) return 0;
+    unsigned __int128 c[OR_MAX_ACC + 1] = {0}, nc[OR_MAX_ACC + 1];
+    c[0] = 1;
+    for (int i = 0; i < d; i++) {
+        for (int K = 0; K <= L; K++) nc[K] = 0;
+        for (int K = 0; K <= L; K++)
+            for (int k = 0; k + K <= L; k++)
+                nc[K + k] += c[K] * (unsigned __int128)(level_nodes(kind, k + 1) - level_nodes(kind, k));
+        for (int K = 0; K <= L; K++) c[K] = nc[K];
+    }
+    unsigned __int128 tot = 0;
+    for (int K = 0; K <= L; K++) tot += c[K];
     return (uint64_t)tot;
 }
 

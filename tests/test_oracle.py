@@ -371,3 +371,115 @@ def test_gradient_cfg5_subset_matches_dp():
                     dp_pin.smolyak_gradient(c["rule"], c["fam"], c["params"], c["d"], c["L"], idx)])
     g = np.ldexp(g, r.exp2)
     assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# Gauss-Patterson rules (Eq. 2.12) and the accuracy-level growth of Section 5.4
+# ---------------------------------------------------------------------------
+
+GP, SLOW = oracle.GP, oracle.SLOW
+
+
+def _gp_degree(level):
+    # Patterson's extensions: 2^g - 1 nodes exact to degree 3 * 2^(g-1) - 1
+    return 1 if level == 1 else 3 * 2 ** (level - 1) - 1
+
+
+@pytest.mark.parametrize("level", range(1, 8))
+def test_gp_rule_exactness_and_shape(level):
+    x, w = oracle.rule(GP, level)
+    n = 2 ** level - 1
+    assert x.size == n and np.all(np.diff(x) > 0) and np.all(w > 0)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.all(np.abs(x + x[::-1] - 1.0) <= 2.3e-16)
+    assert np.all(np.abs(w - w[::-1]) <= 4 * np.finfo(float).eps * w)
+    t = 2.0 * x - 1.0
+    deg = _gp_degree(level)
+    for k in range(deg + 1):
+        exact = 1.0 / (k + 1) if k % 2 == 0 else 0.0
+        assert abs(np.dot(w, t ** k) - exact) < 2e-15, (level, k)
+    if level <= 4:  # the next even degree is missed by a visible margin there
+        k = deg + 1
+        assert abs(np.dot(w, t ** k) - 1.0 / (k + 1)) > 1e-9
+
+
+def test_gp_rules_nest_and_start_from_gauss():
+    # level 2 is the 3-point Gauss-Legendre rule (independent: numpy)
+    x, w = oracle.rule(GP, 2)
+    gx, gw = np.polynomial.legendre.leggauss(3)
+    assert np.allclose(x, (gx + 1) / 2, atol=2e-16, rtol=0)
+    assert np.allclose(w, gw / 2, atol=2e-16, rtol=0)
+    # every level keeps the previous one's nodes, bit for bit, at odd indices
+    for level in range(2, 8):
+        x0, _ = oracle.rule(GP, level - 1)
+        x1, _ = oracle.rule(GP, level)
+        assert np.array_equal(x1[1::2], x0)
+
+
+def test_paper_accuracy_level_sequences():
+    # Section 5.4: the node counts N per accuracy level q = 1..10
+    assert [oracle.rule(GP | SLOW, l)[0].size for l in range(1, 11)] == [1, 3, 3, 7, 7, 7, 15, 15, 15, 15]
+    for kind in (CC, TRAP):
+        assert [oracle.rule(kind | SLOW, l)[0].size for l in range(1, 11)] == [1, 3, 5, 9, 9, 17, 17, 17, 17, 33]
+    # Gauss-Legendre keeps n_l = l
+    assert [oracle.rule(GL | SLOW, l)[0].size for l in range(1, 8)] == list(range(1, 8))
+    # consecutive levels on the same rule have a zero difference rule
+    assert oracle.delta_rule(GP | SLOW, 3)[0].size == 0
+    assert oracle.delta_rule(CC | SLOW, 5)[0].size == 0
+
+
+@pytest.mark.parametrize("kind", [GP, GP | SLOW, CC | SLOW, TRAP | SLOW])
+def test_nested_distinct_count_is_the_merged_point_set(kind):
+    # the closed count of distinct points against merging the enumerated grid
+    for d, L in [(1, 6), (2, 5), (2, 9), (3, 4), (4, 3)]:
+        if oracle.count_distinct(kind, d, L) == 0:
+            continue
+        X, W = oracle.points(kind, d, L, oracle.FORM_COMB)
+        assert len(_merge(X, W)) == oracle.count_distinct(kind, d, L), (kind, d, L)
+
+
+def test_paper_gp_node_counts():
+    path = os.path.join(GOLDEN, "paper_gp_node_counts.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 30
+    for table, d, k, count in rows:
+        assert oracle.count_distinct(GP | SLOW, int(d), int(k) - 1) == int(count), (table, d, k)
+
+
+def test_paper_gp_exp_errors():
+    # Tables 4.1 / 4.3: relative errors of exp(5 |x|^2) on [-1,1]^d
+    mp.mp.dps = 40
+    I1 = mp.quad(lambda y: mp.exp(20 * (y - 0.5) ** 2), [0, 0.5, 1])
+    path = os.path.join(GOLDEN, "paper_gp_exp_errors.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for table, d, k, printed in rows:
+        d, L, printed = int(d), int(k) - 1, float(printed)
+        p = np.array([-20.0] * d + [0.5] * d)
+        r = oracle.integrate(GP | SLOW, si.FAM_GAUSSIAN_LIN, p, d, L)
+        q = mp.mpf(r.mant) * mp.mpf(2) ** r.exp2
+        rel = float(abs(q - I1 ** d) / I1 ** d)
+        assert abs(rel - printed) <= 2e-6 + 5e-5 * printed, (table, d, k, rel, printed)
+
+
+@pytest.mark.parametrize("kind,d,L", [(GP, 2, 3), (GP, 3, 2), (GP | SLOW, 2, 5), (GP | SLOW, 3, 3),
+                                      (CC | SLOW, 3, 3)])
+def test_gp_polynomial_exactness(kind, d, L):
+    # level l exact to degree 2l - 1 in one dimension (both growths) makes the
+    # Smolyak rule exact to total degree 2L + 1 (Novak & Ritter 1996)
+    for form in (oracle.FORM_DIFF, oracle.FORM_COMB):
+        X, W = oracle.points(kind, d, L, form)
+        for deg in range(2 * L + 2):
+            for alpha in _monomials(d, deg):
+                val = np.dot(W, np.prod(X ** np.array(alpha), axis=1))
+                exact = np.prod([1.0 / (a + 1) for a in alpha])
+                assert abs(val - exact) < 1e-13, (kind, d, L, alpha)
+
+
+@pytest.mark.parametrize("kind", [GP, GP | SLOW, CC | SLOW])
+def test_gp_difference_form_equals_combination_form(kind):
+    for fam in (si.FAM_EXP_LINEAR, si.FAM_OSCILLATORY, si.FAM_GAUSSIAN):
+        p = si.item_params(fam, 5, 300 + fam)
+        a = oracle.integrate(kind, fam, p, 5, 4, oracle.FORM_DIFF)
+        b = oracle.integrate(kind, fam, p, 5, 4, oracle.FORM_COMB)
+        qa, qb = a.mant * 2.0 ** a.exp2, b.mant * 2.0 ** b.exp2
+        assert abs(qa - qb) <= 1e-13 * abs(qb), (kind, fam)
