@@ -68,8 +68,19 @@ typedef enum {
 typedef enum {
     SG_RULE_TRAPEZOID = 1,        /* Eq. 2.10; level 1 = midpoint (reading of the paper) */
     SG_RULE_CLENSHAW_CURTIS = 2,  /* Eq. 2.11; n_1 = 1, n_l = 2^(l-1) + 1, nested */
+    SG_RULE_GAUSS_PATTERSON = 3,  /* Eq. 2.12; n_l = 2^l - 1 (members up to 63 nodes), nested */
     SG_RULE_GAUSS_LEGENDRE = 4    /* Eq. 2.13; n_l = l, not nested */
 } sg_rule_kind;
+
+/* How the 1-D level l maps to a member of the rule family. */
+typedef enum {
+    SG_GROWTH_STANDARD = 0,  /* level l is the l-th member (the n_l of sg_rule_kind) */
+    SG_GROWTH_SLOW = 1       /* Section 5.4's accuracy levels: level l is the smallest member
+                                exact for polynomials of degree 2l - 1, so the trapezoid and
+                                Clenshaw-Curtis rules have N = 1, 3, 5, 9, 9, 17, 17, 17, 17, 33
+                                and Gauss-Patterson N = 1, 3, 3, 7, 7, 7, 15, ...; Gauss-Legendre
+                                is unchanged.  Levels that repeat a member add nothing. */
+} sg_growth;
 
 typedef enum {
     SG_FAM_EXP_LINEAR = 0,
@@ -124,14 +135,24 @@ typedef struct {
 } sg_dev_result;
 
 /*
- * Builds the 1-D rule tables of Eqs. 2.10, 2.11 or 2.13 on [0,1] for levels
- * 1..max_level (host and device copies on the current device).  The
+ * Builds the 1-D rule tables of Eqs. 2.10, 2.11, 2.12 or 2.13 on [0,1] for
+ * levels 1..max_level (host and device copies on the current device).  The
  * handle may be used with any d and q with q - d + 1 <= max_level.
  * Limits: 1 <= max_level <= 13 (4097 nodes for the nested rules).
  * Errors: SG_EINVAL (bad kind, NULL out), SG_ERANGE (max_level), SG_ENOMEM,
  * SG_ECUDA.
  */
 SG_API sg_status sg_rule_init(sg_rule_kind kind, int max_level, sg_rule *out);
+
+/*
+ * As sg_rule_init, for the rule of Eq. 2.12 too and with a choice of level
+ * growth (sg_growth).  The paper's Tables 4.1-4.9 and 5.1-5.5 use
+ * SG_RULE_GAUSS_PATTERSON with SG_GROWTH_SLOW, their accuracy level k being
+ * q = d + k - 1.  Limits: 1 <= max_level <= 13, and every level up to
+ * max_level must have a member (Gauss-Patterson with standard growth:
+ * max_level <= 6).  Errors as sg_rule_init; SG_EINVAL for a bad growth.
+ */
+SG_API sg_status sg_rule_init_growth(sg_rule_kind kind, sg_growth growth, int max_level, sg_rule *out);
 
 /* Frees a handle from sg_rule_init.  NULL is accepted. */
 SG_API sg_status sg_rule_destroy(sg_rule rule);
@@ -283,6 +304,7 @@ SG_API sg_status sg_eval_functions(int kind, sg_precision prec, const double *d_
  * record, like sg_integrate_async, and uses the telescoped form.  Its device
  * scratch is one fixed array of about 4.2 MB inside the library, held by
  * every GPU that loads the library until the process exits.
+ * Rules: the four kinds with standard growth (Gauss-Patterson: q - d <= 5).
  * Limits: 1 <= d <= 1024, 0 <= q - d <= 6, at most 131072 table entries
  * (d times the summed node counts of the rule blocks) and 65536 work chunks;
  * larger problems return SG_ERANGE.  The first call on a device (with that

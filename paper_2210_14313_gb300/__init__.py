@@ -19,7 +19,8 @@ import numpy as np
 from ._build import LIB as _LIB_PATH, build as _build_lib
 
 # enums of include/sg.h
-RULE_TRAPEZOID, RULE_CLENSHAW_CURTIS, RULE_GAUSS_LEGENDRE = 1, 2, 4
+RULE_TRAPEZOID, RULE_CLENSHAW_CURTIS, RULE_GAUSS_PATTERSON, RULE_GAUSS_LEGENDRE = 1, 2, 3, 4
+GROWTH_STANDARD, GROWTH_SLOW = 0, 1
 FAM_EXP_LINEAR, FAM_OSCILLATORY, FAM_PRODUCT_PEAK, FAM_GAUSSIAN, FAM_GAUSSIAN_LIN = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED, PREC_FF = 0, 1, 2
 FORM_AUTO, FORM_DIFFERENCE, FORM_TELESCOPED, FORM_COMBINATION = 0, 1, 2, 3
@@ -29,7 +30,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ERANGE", 3: "SG_ENOMEM", 4: "
                 5: "SG_ETIMEOUT", 6: "SG_EUNSUPPORTED"}
 
 # every function include/sg.h declares
-ABI_SYMBOLS = ["sg_rule_init", "sg_rule_destroy", "sg_rule_nodes", "sg_count_points",
+ABI_SYMBOLS = ["sg_rule_init", "sg_rule_init_growth", "sg_rule_destroy", "sg_rule_nodes", "sg_count_points",
                "sg_integrate", "sg_integrate_async", "sg_integrate_batch", "sg_integrate_grad",
                "sg_status_string", "sg_get_tuning", "sg_set_tuning", "sg_autotune",
                "sg_profile_begin", "sg_profile_end", "sg_ceiling", "sg_integrate_noalloc",
@@ -78,6 +79,7 @@ def load(build_if_missing: bool = True):
     lib = ctypes.CDLL(_LIB_PATH)
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
     lib.sg_rule_init.argtypes = [ip, ip, ctypes.POINTER(vp)]
+    lib.sg_rule_init_growth.argtypes = [ip, ip, ip, ctypes.POINTER(vp)]
     lib.sg_rule_destroy.argtypes = [vp]
     lib.sg_rule_nodes.argtypes = [vp, ip, dp, dp, ctypes.POINTER(ctypes.c_int)]
     lib.sg_count_points.argtypes = [vp, ip, ip, ip, ctypes.POINTER(ctypes.c_uint64),
@@ -130,16 +132,18 @@ def _require_cuda():
 
 
 class Rule:
-    """A 1-D rule family (trapezoid / Clenshaw-Curtis / Gauss-Legendre) with
-    device tables for levels 1..max_level."""
+    """A 1-D rule family (trapezoid / Clenshaw-Curtis / Gauss-Patterson /
+    Gauss-Legendre) with device tables for levels 1..max_level; ``growth``
+    GROWTH_SLOW selects the paper's accuracy levels (Section 5.4)."""
 
-    def __init__(self, kind: int, max_level: int = 8):
+    def __init__(self, kind: int, max_level: int = 8, growth: int = GROWTH_STANDARD):
         _require_cuda()
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.sg_rule_init(kind, max_level, ctypes.byref(h)), "sg_rule_init")
+        _check(lib.sg_rule_init_growth(kind, growth, max_level, ctypes.byref(h)), "sg_rule_init_growth")
         self.handle = h
         self.kind = kind
+        self.growth = growth
         self.max_level = max_level
 
     def nodes(self, level: int):

@@ -93,12 +93,20 @@ static sg_status dev_ctx(DevCtx **out) {
 // ---------------------------------------------------------------------------
 
 extern "C" sg_status sg_rule_init(sg_rule_kind kind, int max_level, sg_rule *out) {
+    return sg_rule_init_growth(kind, SG_GROWTH_STANDARD, max_level, out);
+}
+
+extern "C" sg_status sg_rule_init_growth(sg_rule_kind kind, sg_growth growth, int max_level, sg_rule *out) {
     if (!out || (kind != SG_RULE_TRAPEZOID && kind != SG_RULE_CLENSHAW_CURTIS &&
-                 kind != SG_RULE_GAUSS_LEGENDRE))
+                 kind != SG_RULE_GAUSS_PATTERSON && kind != SG_RULE_GAUSS_LEGENDRE))
         return SG_EINVAL;
+    if (growth != SG_GROWTH_STANDARD && growth != SG_GROWTH_SLOW) return SG_EINVAL;
     if (max_level < 1 || max_level > SG_MAX_LEVEL) return SG_ERANGE;
+    const int ikind = (int)kind | (growth == SG_GROWTH_SLOW ? SG_KIND_SLOW : 0);
+    for (int l = 1; l <= max_level; l++)
+        if (sg_level_nodes(ikind, l) == 0) return SG_ERANGE;
     sg_rule_s *r = new sg_rule_s();
-    r->kind = kind;
+    r->kind = ikind;
     r->max_level = max_level;
     if (cudaGetDevice(&r->device) != cudaSuccess) {
         delete r;
@@ -108,7 +116,7 @@ extern "C" sg_status sg_rule_init(sg_rule_kind kind, int max_level, sg_rule *out
     std::vector<double2> all;
     for (int bk = 0; bk < 3; bk++)
         for (int k = 1; k < max_level; k++) {
-            int n = sg_block(kind, bk, k, tx.data(), tw.data());
+            int n = sg_block(ikind, bk, k, tx.data(), tw.data());
             r->x[bk][k].assign(tx.begin(), tx.begin() + n);
             r->w[bk][k].assign(tw.begin(), tw.begin() + n);
             r->off[bk][k] = (int)all.size();
@@ -632,6 +640,7 @@ extern "C" sg_status sg_count_points(sg_rule rule, int d, int q, sg_form form, u
     if (evals) {
         std::vector<PatSpec> specs;
         gen_patterns(form, d, L, specs);
+        drop_empty_patterns(rule, specs);
         unsigned __int128 tot = 0;
         for (auto &sp : specs) {
             unsigned __int128 v = binom128(d, sp.r);

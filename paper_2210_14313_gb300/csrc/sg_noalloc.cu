@@ -166,9 +166,12 @@ int na_block(int kind, bool delta, int k, double2 *xw, int cap) {
     }
     if (n1 > cap) return 0;
     for (int j = 0; j < n1; j++) xw[j] = make_double2(x1[j], w1[j]);
+    // nested: node j of level k is node 2j of level k+1 (trapezoid, Clenshaw-
+    // Curtis) or node 2j + 1 (Gauss-Patterson)
+    const int shift = kind == SG_RULE_GAUSS_PATTERSON ? 1 : 0;
     if (n0 == 1) xw[n1 / 2].y -= w0[0];
     else
-        for (int j = 0; j < n0; j++) xw[2 * j].y -= w0[j];  // nested: node j of level k is node 2j of k+1
+        for (int j = 0; j < n0; j++) xw[2 * j + shift].y -= w0[j];
     return n1;
 }
 
@@ -328,7 +331,8 @@ extern "C" sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, cons
                                           int d, int q, sg_precision prec, void *stream,
                                           sg_dev_result *d_out) {
     if (!d_params || !d_out) return SG_EINVAL;
-    if (kind != SG_RULE_TRAPEZOID && kind != SG_RULE_CLENSHAW_CURTIS && kind != SG_RULE_GAUSS_LEGENDRE)
+    if (kind != SG_RULE_TRAPEZOID && kind != SG_RULE_CLENSHAW_CURTIS && kind != SG_RULE_GAUSS_PATTERSON &&
+        kind != SG_RULE_GAUSS_LEGENDRE)
         return SG_EINVAL;
     if ((int)fam < 0 || (int)fam > 4 || (prec != SG_PREC_FP64 && prec != SG_PREC_MIXED)) return SG_EINVAL;
     if (d < 1 || q < d) return SG_EINVAL;

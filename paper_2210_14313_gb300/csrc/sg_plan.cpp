@@ -88,6 +88,19 @@ void gen_patterns(int form, int d, int L, std::vector<PatSpec> &out) {
 
 int tab_m(sg_rule rule, BlockRef b) { return (int)rule->x[b.bk][b.k].size(); }
 
+// Patterns with an empty block (a difference rule between two levels that use
+// the same member of a slowly growing rule) contribute nothing.
+void drop_empty_patterns(sg_rule rule, std::vector<PatSpec> &specs) {
+    specs.erase(std::remove_if(specs.begin(), specs.end(),
+                               [&](const PatSpec &sp) {
+                                   if (tab_m(rule, sp.tail) == 0) return true;
+                                   for (int t = 0; t < sp.r - 1; t++)
+                                       if (tab_m(rule, sp.pre[t]) == 0) return true;
+                                   return false;
+                               }),
+                specs.end());
+}
+
 // n_d^q of Eq. 2.6: sum over the combination-form multi-indices of
 // prod n_{l_i}, as a polynomial in the excess, direction by direction.
 bool count_points(int kind, int d, int L, u64 *out) {
@@ -162,6 +175,7 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
             b.L = L_item;
             b.form = R.form;
             gen_patterns(R.form, d_item, L_item, b.specs);
+            drop_empty_patterns(rule, b.specs);
             ib.push_back(b);
         };
         new_item(SG_ROLE_FORWARD, -1, 0.0, R.d, -1, R.L, g);

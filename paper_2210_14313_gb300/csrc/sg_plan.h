@@ -92,6 +92,7 @@ unsigned __int128 binom128(long long n, int k);
 void gen_patterns(int form, int d, int L, std::vector<PatSpec> &out);
 // Nodes per direction of a rule block.
 int tab_m(sg_rule rule, BlockRef b);
+void drop_empty_patterns(sg_rule rule, std::vector<PatSpec> &specs);
 // n_d^q of Eq. 2.6 (false if beyond 64 bits).
 bool count_points(int kind, int d, int L, u64 *out);
 // Builds the host arrays of a plan; device fields stay empty.

@@ -56,3 +56,23 @@ def unrank_mismatches(d, r, n=2000):
     lib.chk_unrank.restype = ctypes.c_longlong
     lib.chk_unrank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
     return lib.chk_unrank(d, r, n)
+
+
+def rule(kind, level):
+    """The library's level-``level`` rule on [0,1] (kind may carry the slow-growth flag 16)."""
+    lib = _load()
+    x = np.zeros(2 * 4097 + 2)
+    w = np.zeros(2 * 4097 + 2)
+    dp = ctypes.POINTER(ctypes.c_double)
+    n = lib.chk_rule(kind, level, x.ctypes.data_as(dp), w.ctypes.data_as(dp))
+    return x[:n].copy(), w[:n].copy()
+
+
+def block(kind, bk, k):
+    """The library's rule block (0 difference, 1 full, 2 telescoped tail) at excess k."""
+    lib = _load()
+    x = np.zeros(2 * 4097 + 2)
+    w = np.zeros(2 * 4097 + 2)
+    dp = ctypes.POINTER(ctypes.c_double)
+    n = lib.chk_block(kind, bk, k, x.ctypes.data_as(dp), w.ctypes.data_as(dp))
+    return x[:n].copy(), w[:n].copy()

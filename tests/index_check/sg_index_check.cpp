@@ -328,4 +328,8 @@ long long chk_unrank(int d, int r, long long n) {
     }
     return bad;
 }
+
+// The library's level rule and blocks, built on the host (no device needed).
+int chk_rule(int kind, int level, double *x, double *w) { return sg_rule_level(kind, level, x, w); }
+int chk_block(int kind, int bk, int k, double *x, double *w) { return sg_block(kind, bk, k, x, w); }
 }

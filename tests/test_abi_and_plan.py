@@ -45,7 +45,9 @@ def test_invalid_arguments_rejected_without_gpu():
     import ctypes
     import paper_2210_14313_gb300 as sg
     lib = sg.load()
-    assert lib.sg_rule_init(3, 4, ctypes.byref(ctypes.c_void_p())) == 1       # bad rule kind
+    assert lib.sg_rule_init(5, 4, ctypes.byref(ctypes.c_void_p())) == 1       # bad rule kind
+    assert lib.sg_rule_init_growth(2, 7, 4, ctypes.byref(ctypes.c_void_p())) == 1  # bad growth
+    assert lib.sg_rule_init_growth(3, 0, 7, ctypes.byref(ctypes.c_void_p())) == 2  # no 127-node member
     assert lib.sg_rule_init(2, 0, ctypes.byref(ctypes.c_void_p())) == 2       # level out of range
     assert lib.sg_rule_init(2, 4, None) == 1
     assert lib.sg_integrate(None, 0, None, 0, 4, 9, 0, 0, None, None) == 1
@@ -69,7 +71,13 @@ CASES += [dict(name="ragged%d" % k, **it) for k, it in enumerate(si.batch(n=8, s
 CASES += [dict(name="d1", rule=2, fam=3, d=1, L=6, params=si.item_params(3, 1, 5)),
           dict(name="L0", rule=4, fam=1, d=7, L=0, params=si.item_params(1, 7, 6)),
           dict(name="d_lt_L", rule=4, fam=2, d=2, L=6, params=si.item_params(2, 2, 7)),
-          dict(name="trap", rule=1, fam=0, d=5, L=4, params=si.item_params(0, 5, 8))]
+          dict(name="trap", rule=1, fam=0, d=5, L=4, params=si.item_params(0, 5, 8)),
+          # Gauss-Patterson (Eq. 2.12) and the Section 5.4 accuracy levels (flag 16)
+          dict(name="gp", rule=3, fam=1, d=5, L=4, params=si.item_params(1, 5, 9)),
+          dict(name="gp_slow_test3", rule=3 | 16, fam=4, d=6, L=9, params=np.array([2.0] * 6 + [0.5] * 6)),
+          dict(name="gp_slow_peak", rule=3 | 16, fam=2, d=4, L=8, params=si.item_params(2, 4, 10)),
+          dict(name="cc_slow", rule=2 | 16, fam=3, d=6, L=6, params=si.item_params(3, 6, 11)),
+          dict(name="trap_slow", rule=1 | 16, fam=0, d=4, L=5, params=si.item_params(0, 4, 12))]
 
 
 @pytest.mark.parametrize("form", [1, 2, 3])
@@ -107,3 +115,31 @@ def test_n_d_q_matches_oracle_count():
         r = index_check.run(c["rule"], c["fam"], c["params"], c["d"], c["L"], form=3)
         centre = 1 if c["d"] > c["L"] else 0
         assert r["evals"] == oracle.count_points(c["rule"], c["d"], c["L"]) - centre
+
+
+@pytest.mark.parametrize("member", range(1, 7))
+def test_library_gauss_patterson_matches_oracle_table(member):
+    # two independent constructions: the library's double-double Newton
+    # iteration and the oracle's 300-digit table (gen_gp_table.py)
+    x, w = index_check.rule(3, member)
+    xo, wo = oracle.rule(oracle.GP, member)
+    assert x.size == xo.size == 2 ** member - 1
+    assert np.all(np.abs(x - xo) <= np.spacing(np.maximum(xo, 1e-300)))
+    assert np.all(np.abs(w - wo) <= 4e-16 * wo)
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 4])
+def test_library_growth_matches_oracle(kind):
+    for growth in (0, 16):
+        top = 13 if (growth or kind != 3) else 6
+        for level in range(1, top + 1):
+            n = index_check.rule(kind | growth, level)[0].size
+            assert n == oracle.rule(kind | growth, level)[0].size, (kind, growth, level)
+        for k in range(1, top):
+            xb, wb = index_check.block(kind | growth, 0, k)
+            xo, wo = oracle.delta_rule(kind | growth, k + 1)
+            assert xb.size == xo.size, (kind, growth, k)
+            if xb.size:
+                order, order_o = np.argsort(xb, kind="stable"), np.argsort(xo, kind="stable")
+                assert np.allclose(xb[order], xo[order_o], rtol=0, atol=4e-16)
+                assert np.allclose(wb[order], wo[order_o], rtol=0, atol=1e-14 * np.abs(wo).max())

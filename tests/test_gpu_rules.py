@@ -1,0 +1,93 @@
+"""GPU parity for the Gauss-Patterson rule (Eq. 2.12) and the accuracy-level
+growth of Section 5.4 (SG_GROWTH_SLOW), through the C ABI, against the CPU
+oracle; plus two rows of the paper's Gaussian test (Tables 4.5 / 4.6)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2210_14313_gb300 as sg  # noqa: E402
+
+GP, SLOW = sg.RULE_GAUSS_PATTERSON, oracle.SLOW
+
+
+@pytest.fixture(scope="module")
+def rules():
+    out = {}
+    for kind in (1, 2, 3):
+        out[(kind, 0)] = sg.Rule(kind, max_level=6 if kind == 3 else 10)
+        out[(kind, 1)] = sg.Rule(kind, max_level=13, growth=sg.GROWTH_SLOW)
+    return out
+
+
+def rel_err(r, o):
+    return abs(r.mant * 2.0 ** (r.exp2 - o.exp2) - o.mant) / abs(o.mant)
+
+
+# (rule, growth, family, d, L, params)
+CASES = [
+    (GP, 0, si.FAM_OSCILLATORY, 5, 4, si.item_params(si.FAM_OSCILLATORY, 5, 21)),
+    (GP, 0, si.FAM_PRODUCT_PEAK, 12, 3, si.item_params(si.FAM_PRODUCT_PEAK, 12, 22)),
+    (GP, 1, si.FAM_GAUSSIAN, 8, 9, si.item_params(si.FAM_GAUSSIAN, 8, 23)),
+    (GP, 1, si.FAM_EXP_LINEAR, 4, 12, si.item_params(si.FAM_EXP_LINEAR, 4, 24)),
+    (2, 1, si.FAM_OSCILLATORY, 6, 6, si.item_params(si.FAM_OSCILLATORY, 6, 25)),
+    (1, 1, si.FAM_GAUSSIAN_LIN, 5, 5, si.item_params(si.FAM_GAUSSIAN_LIN, 5, 26)),
+]
+
+
+def _ids(c):
+    return "r%d_g%d_f%d_d%d_L%d" % c[:5]
+
+
+@pytest.mark.parametrize("c", CASES, ids=_ids)
+def test_fp64_and_float_float(rules, c):
+    kind, growth, fam, d, L, p = c
+    o = oracle.integrate(kind | (SLOW if growth else 0), fam, p, d, L)
+    rule = rules[(kind, growth)]
+    for form in (sg.FORM_TELESCOPED, sg.FORM_DIFFERENCE):
+        r = sg.integrate(rule, fam, p, d, d + L, prec=sg.PREC_FP64, form=form)
+        assert rel_err(r, o) <= 1e-12, (form, rel_err(r, o))
+    assert r.points == oracle.count_points(kind | (SLOW if growth else 0), d, L)
+    r = sg.integrate(rule, fam, p, d, d + L, prec=sg.PREC_FF)
+    assert rel_err(r, o) <= 1e-9
+
+
+def test_rule_nodes_through_the_abi(rules):
+    for member in range(1, 7):
+        x, w = rules[(GP, 0)].nodes(member)
+        xo, wo = oracle.rule(GP, member)
+        assert np.array_equal(x, xo) or np.max(np.abs(x - xo)) <= 2.3e-16
+        assert np.max(np.abs(w - wo) / wo) <= 4e-16
+    for level in range(1, 14):
+        assert rules[(GP, 1)].nodes(level)[0].size == oracle.rule(GP | SLOW, level)[0].size
+
+
+@pytest.mark.parametrize("d,k,printed", [(10, 10, 1.6855e-6), (8, 12, 4.0881e-8)])
+def test_paper_gaussian_rows(rules, d, k, printed):
+    # Test 3 (Section 4.2): (2 pi)^(-1/2) exp(-|x|^2 / 2) on [-1,1]^d, Gauss-
+    # Patterson with accuracy level k; on [0,1]^d the gaussian-lin family with
+    # a_i = 2, u_i = 1/2 (constant factors cancel in the relative error).  The
+    # printed errors grow like d * 5e-9 (an inexact reference value), so the
+    # GPU value is held to the oracle at 1e-12 and to the exact integral at the
+    # printed error.
+    # These sums cancel strongly (kappa = sum |W D| / |Q| is 4e4 at d = 10,
+    # k = 10): each point's deviation carries a rounding of order u, so the FP64
+    # fold is held to max(1e-12, 2 u kappa) here (the oracle, which sums with
+    # compensation, is within 7e-14 of the 40-digit separable value there).
+    p = np.array([2.0] * d + [0.5] * d)
+    r = sg.integrate(rules[(GP, 1)], si.FAM_GAUSSIAN_LIN, p, d, d + k - 1, prec=sg.PREC_FP64)
+    o = oracle.integrate(GP | SLOW, si.FAM_GAUSSIAN_LIN, p, d, k - 1)
+    assert rel_err(r, o) <= max(1e-12, 2 * 2.0 ** -53 * o.cond)
+    # exact: prod_i int_0^1 exp(-2 (y - 1/2)^2) dy = (sqrt(pi/2) erf(1/sqrt(2)))^d
+    exact = (math.sqrt(math.pi / 2.0) * math.erf(1.0 / math.sqrt(2.0))) ** d
+    q = r.mant * 2.0 ** r.exp2
+    assert abs(q - exact) / exact <= printed
