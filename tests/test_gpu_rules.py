@@ -77,9 +77,8 @@ def test_paper_gaussian_rows(rules, d, k, printed):
     # Patterson with accuracy level k; on [0,1]^d the gaussian-lin family with
     # a_i = 2, u_i = 1/2 (constant factors cancel in the relative error).  The
     # printed errors grow like d * 5e-9 (an inexact reference value), so the
-    # GPU value is held to the oracle at 1e-12 and to the exact integral at the
-    # printed error.
-    # These sums cancel strongly (kappa = sum |W D| / |Q| is 4e4 at d = 10,
+    # GPU value is held to the oracle, and to the exact integral at the printed
+    # error.  These sums cancel strongly (kappa = sum |W D| / |Q| is 4e4 at d = 10,
     # k = 10): each point's deviation carries a rounding of order u, so the FP64
     # fold is held to max(1e-12, 2 u kappa) here (the oracle, which sums with
     # compensation, is within 7e-14 of the 40-digit separable value there).
