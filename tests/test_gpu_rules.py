@@ -71,16 +71,17 @@ def test_rule_nodes_through_the_abi(rules):
         assert rules[(GP, 1)].nodes(level)[0].size == oracle.rule(GP | SLOW, level)[0].size
 
 
-@pytest.mark.parametrize("d,k,printed", [(10, 10, 1.6855e-6), (8, 12, 4.0881e-8)])
+@pytest.mark.parametrize("d,k,printed", [(10, 10, 1.6855e-6), (12, 10, 1.8074e-5)])
 def test_paper_gaussian_rows(rules, d, k, printed):
     # Test 3 (Section 4.2): (2 pi)^(-1/2) exp(-|x|^2 / 2) on [-1,1]^d, Gauss-
     # Patterson with accuracy level k; on [0,1]^d the gaussian-lin family with
-    # a_i = 2, u_i = 1/2 (constant factors cancel in the relative error).  The
-    # printed errors grow like d * 5e-9 (an inexact reference value), so the
-    # GPU value is held to the oracle, and to the exact integral at the printed
-    # error.  These sums cancel strongly (kappa = sum |W D| / |Q| is 4e4 at d = 10,
-    # k = 10): each point's deviation carries a rounding of order u, so the FP64
-    # fold is held to max(1e-12, 2 u kappa) here (the oracle, which sums with
+    # a_i = 2, u_i = 1/2 (constant factors cancel in the relative error).  Of
+    # Table 4.5's error column only the rows far above 1e-6 reproduce (to 1.3%
+    # and 1.6%); the smaller printed values sit near d * 5e-9 whatever the
+    # exact Smolyak error is, so they are not used.  These sums cancel
+    # strongly (kappa = sum |W D| / |Q| is 4e4 at d = 10): each point's
+    # deviation carries a rounding of order u, so the FP64 fold is held to the
+    # oracle at max(1e-12, 2 u kappa) (the oracle, which sums with
     # compensation, is within 7e-14 of the 40-digit separable value there).
     p = np.array([2.0] * d + [0.5] * d)
     r = sg.integrate(rules[(GP, 1)], si.FAM_GAUSSIAN_LIN, p, d, d + k - 1, prec=sg.PREC_FP64)
@@ -89,4 +90,4 @@ def test_paper_gaussian_rows(rules, d, k, printed):
     # exact: prod_i int_0^1 exp(-2 (y - 1/2)^2) dy = (sqrt(pi/2) erf(1/sqrt(2)))^d
     exact = (math.sqrt(math.pi / 2.0) * math.erf(1.0 / math.sqrt(2.0))) ** d
     q = r.mant * 2.0 ** r.exp2
-    assert abs(q - exact) / exact <= printed
+    assert abs(abs(q - exact) / exact / printed - 1.0) <= 0.03
