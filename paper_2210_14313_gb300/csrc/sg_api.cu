@@ -502,6 +502,7 @@ static SgLaunchCfg fold_cfg(const Plan *P, int prec, DevCtx *C) {
     const long long need = (long long)((P->nchunks + c.warps_per_cta - 1) / c.warps_per_cta);
     if (need < ctas) ctas = std::max<long long>(need, 1);
     c.ctas = (int)ctas;
+    c.dependent = P->nchunks <= SG_DEPENDENT_LAUNCH_MAX_CHUNKS ? 1 : 0;
     return c;
 }
 

@@ -148,6 +148,24 @@ struct SgFlatPos {
     }
 };
 
+// Lane layout of the float fold: lane l takes tail entries e0, e0 + estep,
+// ... and for each of them prefix tuples a0, a0 + astep, ...  With a tail of
+// E >= 32 entries the whole warp shares every tuple (estep = 32, astep = 1);
+// a shorter tail splits the warp into 32 / E groups of E lanes, group g
+// taking tuples g, g + 32/E, ...; lanes beyond the last whole group idle.
+struct SgLaneGroups {
+    int e0, estep, a0, astep;
+    bool active;
+    SG_HD SgLaneGroups(int lane, int E) {
+        const int G = E >= 32 ? 1 : 32 / E, Eg = E >= 32 ? 32 : E;
+        a0 = lane / Eg;
+        e0 = lane - a0 * Eg;
+        estep = Eg;
+        astep = G;
+        active = a0 < G;
+    }
+};
+
 // Table entry of prefix position t for prefix node tuple q (mixed radix over
 // the prefix block sizes, the last prefix position fastest).  Returns the
 // entry offset relative to the item's table and leaves q / m in *q.

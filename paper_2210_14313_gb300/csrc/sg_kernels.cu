@@ -323,46 +323,52 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
                                          T cphi, int lane, FoldAcc &F) {
     typedef typename V2T<T>::type V2;
     const int E = E1 + E2;
-    SgFlatPos f(lane, E);
     if constexpr (sizeof(T) == 4) {
-        // points of this lane; plain float partial sums of 8 points feed the
-        // TwoSum accumulator
-        const long long n = (long long)At * E;
-        const long long iters = lane < n ? (n - 1 - lane) / 32 + 1 : 0;
+        // float (FP32 pipe, charged per warp instruction): lanes take tail
+        // entries, each lane's entry stays in registers while it walks the
+        // prefix tuples; a tail shorter than 32 splits the warp into groups
+        // that take different tuples (SgLaneGroups).  Plain float partial
+        // sums of 8 points feed the TwoSum accumulator.
+        const SgLaneGroups g(lane, E);
+        if (!g.active) return;
         float hs = F.hs, hc = F.hc, habs = F.habs;
-        for (long long g = iters >> 3; g > 0; g--) {
-            float part = 0.f;
+        for (int e = g.e0; e < E; e += g.estep) {
+            const V2 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
+            int a = g.a0;
+            for (; a + 7 * g.astep < At; a += 8 * g.astep) {
+                float part = 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const float2 p = sP[f.a];
-                const V2 te = tail_entry(tab, base1, E1, base2, f.e);
+                for (int u = 0; u < 8; u++) {
+                    const float2 p = sP[a + u * g.astep];
+                    const float W = p.y * te.y;
+                    const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
+                    part = fmaf(W, D, part);
+                    habs = fmaf(fabsf(W), fabsf(D), habs);
+                }
+                float t, err;
+                two_sum(hs, part, t, err);
+                hs = t;
+                hc += err;
+            }
+            float part = 0.f;
+            for (; a < At; a += g.astep) {
+                const float2 p = sP[a];
                 const float W = p.y * te.y;
                 const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
                 part = fmaf(W, D, part);
                 habs = fmaf(fabsf(W), fabsf(D), habs);
-                f.step();
             }
             float t, err;
             two_sum(hs, part, t, err);
             hs = t;
             hc += err;
         }
-        float part = 0.f;
-        for (int u = (int)(iters & 7); u > 0; u--) {
-            const float2 p = sP[f.a];
-            const V2 te = tail_entry(tab, base1, E1, base2, f.e);
-            const float W = p.y * te.y;
-            const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
-            part = fmaf(W, D, part);
-            habs = fmaf(fabsf(W), fabsf(D), habs);
-            f.step();
-        }
-        float t, err;
-        two_sum(hs, part, t, err);
-        F.hs = t;
-        F.hc = hc + err;
+        F.hs = hs;
+        F.hc = hc;
         F.habs = habs;
     } else {
+        // FP64 (charged per active lane): the flat layout
+        SgFlatPos f(lane, E);
         double acc = F.acc;
         for (; f.a < At; f.step()) {
             const double2 p = sP[f.a];
@@ -417,7 +423,8 @@ __device__ __forceinline__ void unrank_warp(unsigned long long rank, int d, int 
 template <typename T, int GK>
 __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                            const SgItemDev *__restrict__ I, unsigned long long c,
-                           typename PrefixState<T>::type *sP, int *sIdx, int lane, FoldAcc &F) {
+                           typename PrefixState<T>::type *sP, int *sIdx, int lane, FoldAcc &F,
+                           bool &waited) {
     typedef typename V2T<T>::type V2;
     const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
     const int d = I->d, r = P->r, skip = I->skip, tm = P->tm;
@@ -427,8 +434,12 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     unrank_warp(rank, d, r, A.binom, sIdx, lane);
     // everything above reads only the plan; the tables and item values come
     // from the setup kernel, which may still be finishing (programmatic
-    // dependent launch)
-    cudaGridDependencySynchronize();
+    // dependent launch).  One wait per warp suffices: once it returns the
+    // setup kernel has finished.
+    if (!waited) {
+        cudaGridDependencySynchronize();
+        waited = true;
+    }
     __syncwarp();
     const SgItemVar *V = A.vars + (I - A.items);
     typedef typename std::conditional<std::is_same<T, FFTag>::value, float, T>::type TS;
@@ -639,6 +650,7 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     PS *sP = (PS *)smem + (size_t)warp * SG_APAD;
     int *sIdx = (int *)(smem + (size_t)nw * SG_APAD * sizeof(PS)) + warp * SG_MAX_R;
+    bool waited = false;
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(A.work, 1ull);
@@ -656,8 +668,8 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         if (A.skip_unflagged && !A.flags[item]) continue;
         const SgItemDev *I = A.items + item;
         FoldAcc F;
-        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sIdx, lane, F);
-        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sIdx, lane, F);
+        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sIdx, lane, F, waited);
+        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sIdx, lane, F, waited);
         double acc, aabs;
         if constexpr (std::is_same<T, double>::value) {
             // the FP64 fold skips |W D| per point: the chunk's |sum| stands in
@@ -949,7 +961,7 @@ cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cf
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
-    lc.numAttrs = 1;
+    lc.numAttrs = cfg.dependent ? 1 : 0;
     if (prec == 2) return cudaLaunchKernelEx(&lc, sg_fold_kernel_x, a);
     if (prec == 1) return cudaLaunchKernelEx(&lc, sg_fold_kernel_f, a);
     return cudaLaunchKernelEx(&lc, sg_fold_kernel_d, a);

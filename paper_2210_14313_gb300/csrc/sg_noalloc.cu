@@ -429,6 +429,7 @@ extern "C" sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, cons
     const long long need = (long long)((P.nchunks + kNaWarps - 1) / kNaWarps);
     if (need < ctas) ctas = need > 0 ? need : 1;
     cfg.ctas = (int)ctas;
+    cfg.dependent = P.nchunks <= SG_DEPENDENT_LAUNCH_MAX_CHUNKS ? 1 : 0;
     NA_CK(sg_launch_fold(fa, p, 0, cfg, s));
 #undef NA_CK
     return SG_OK;

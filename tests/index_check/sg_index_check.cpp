@@ -4,9 +4,9 @@
 // sequentially with the same enumeration primitives the CUDA kernel uses
 // (sg_fold_logic.h): unranking, runs, tail segments, prefix entries.  Every
 // table access is checked against the bounds of the block it must fall in,
-// and the warp's lane split of a run (prefix groups x tail entries) is
-// replayed to check that each (prefix tuple, tail entry) pair is visited
-// exactly once.  The sums are formed in double so that the tests can also
+// and both lane layouts of a run (the flat one of the FP64 and float-float
+// folds, the lane groups of the float fold) are replayed to check that each
+// (prefix tuple, tail entry) pair is visited exactly once.  The sums are formed in double so that the tests can also
 // compare them with the oracle; this is a check of the enumeration, not a
 // second implementation of the method (no CUDA code path calls it).
 #include <math.h>
@@ -245,6 +245,16 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
                 }
                 lane_slots += 32 * passes;
                 for (int v : seen)
+                    if (v != 1) badpairs++;
+                // the float fold's lane groups must cover the same pairs once
+                std::vector<int> seen2((size_t)At * E, 0);
+                for (int lane = 0; lane < 32; lane++) {
+                    const SgLaneGroups lg(lane, E);
+                    if (!lg.active) continue;
+                    for (int e = lg.e0; e < E; e += lg.estep)
+                        for (int a = lg.a0; a < At; a += lg.astep) seen2[(size_t)a * E + e]++;
+                }
+                for (int v : seen2)
                     if (v != 1) badpairs++;
             }
             cnt -= run;
