@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -30,7 +31,7 @@ METRIC = "effective sparse-grid points/sec and s/integral at stated rel. error v
 # summarised in profiles/sg_fold_kernel_d__cfg2_d12_gl_L6_oscillatory.txt.
 # Valid only for the kernel sources with this digest; otherwise reported as
 # null until the capture is taken again.
-_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (105216, "c132d557d8d933e8")}
+_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (88320, "dafd35ac2aa23870")}
 _KERNEL_SOURCES = ["paper_2210_14313_gb300/csrc/sg_kernels.cu", "paper_2210_14313_gb300/csrc/sg_fold_logic.h",
                    "paper_2210_14313_gb300/csrc/sg_ff.cuh", "paper_2210_14313_gb300/csrc/sg_internal.h"]
 
@@ -353,6 +354,87 @@ def sg_family_name(f):
     return {0: "exp_linear", 1: "oscillatory", 2: "product_peak", 3: "gaussian", 4: "gaussian_lin"}[f]
 
 
+def _sweep_params(fam, d):
+    """The integrands of Test 10 (Section 6.2) on [0,1]^d as library families."""
+    import numpy as np
+    if fam == "f1":  # exp(sum (-1)^(i+1) x_i)
+        return 0, np.concatenate([[(-1.0) ** i for i in range(d)], np.zeros(d)])
+    if fam == "f2":  # prod 1 / (0.9^2 + (x_i - 0.6)^2)
+        return 2, np.concatenate([np.full(d, 1 / 0.9), np.full(d, 0.6)])
+    if fam == "f3":  # exp(-|x|^2 / 2) (the constant factor does not change the work)
+        return 3, np.concatenate([np.full(d, math.sqrt(0.5)), np.zeros(d)])
+    # f4: cos(2 pi + sum x_i)
+    return 1, np.concatenate([np.ones(d), [1.0], np.zeros(d - 1)])
+
+
+def _fit(xs, ts):
+    """Least-squares t = c x^b on log scales: (b, c, R^2)."""
+    import numpy as np
+    lx, lt = np.log(np.asarray(xs, float)), np.log(np.asarray(ts, float))
+    b, a = np.polyfit(lx, lt, 1)
+    pred = a + b * lx
+    ss = float(((lt - pred) ** 2).sum()), float(((lt - lt.mean()) ** 2).sum())
+    return float(b), float(math.exp(a)), 1.0 - ss[0] / ss[1] if ss[1] > 0 else 1.0
+
+
+def run_sweep(args):
+    """Section 6's complexity experiment on the GPU: the time of one integral
+    against the dimension d at fixed excess levels L = 2, 3, 4 (and at d = 10
+    for more levels) for the Test 10 integrands, three rules (Clenshaw-Curtis,
+    Gauss-Legendre, Gauss-Patterson with the accuracy-level growth) and two
+    precisions.  One JSON line per measurement (median of 5 blocking calls),
+    then the power-law fits t = c d^b over the runs well above the launch
+    floor and the fits t = t0 + evals / R (launch floor and rate)."""
+    import numpy as np
+    import torch
+    import paper_2210_14313_gb300 as sg
+    torch.cuda.set_device(0)
+    rules = {"cc": sg.Rule(sg.RULE_CLENSHAW_CURTIS, max_level=10),
+             "gl": sg.Rule(sg.RULE_GAUSS_LEGENDRE, max_level=10),
+             "gp": sg.Rule(sg.RULE_GAUSS_PATTERSON, max_level=13, growth=sg.GROWTH_SLOW)}
+    budget = float(args.sweep_budget)
+    series, rates = {}, {}
+    ds = [5, 10, 20, 50, 100, 200, 500, 1000, 2000]
+    for rname, rule in rules.items():
+        for fam in ("f1", "f2", "f3", "f4"):
+            for prec in (sg.PREC_FP64, sg.PREC_MIXED):
+                runs = [(L, d) for L in (2, 3, 4) for d in ds] + [(L, 10) for L in (1, 5, 6, 7, 8)]
+                for L, d in runs:
+                    pts, ev = sg.count_points(rule, d, d + L)
+                    if ev > budget * (1 if prec == sg.PREC_FP64 else 20):
+                        continue
+                    f, p = _sweep_params(fam, d)
+                    for _ in range(2):
+                        sg.integrate(rule, f, p, d, d + L, prec=prec)
+                    t = sorted(sg.integrate(rule, f, p, d, d + L, prec=prec).seconds for _ in range(5))[2]
+                    rec = {"sweep": "complexity", "rule": rname, "integrand": fam,
+                           "prec": {0: "fp64", 1: "mixed"}[prec], "d": d, "L": L, "points": pts,
+                           "evals": ev, "s": t, "points_per_s": pts / t}
+                    print(json.dumps(rec), flush=True)
+                    series.setdefault((rname, fam, rec["prec"], L), []).append((d, t))
+                    rates.setdefault((rname, fam, rec["prec"]), []).append((ev, t))
+    for (rname, fam, prec, L), pts in sorted(series.items()):
+        # power law in d over the runs well above the launch floor
+        floor = min(t for _, t in pts)
+        use = [(x, t) for x, t in pts if t >= 5 * floor]
+        if len(use) < 3:
+            use = sorted(pts)[-3:]
+        if len(use) < 3:
+            continue
+        b, c, r2 = _fit([x for x, _ in use], [t for _, t in use])
+        print(json.dumps({"fit": "t = c d^b", "rule": rname, "integrand": fam, "prec": prec, "L": L,
+                          "b": round(b, 3), "c": c, "r2": round(r2, 4),
+                          "range": [min(x for x, _ in use), max(x for x, _ in use)]}), flush=True)
+    for (rname, fam, prec), pts in sorted(rates.items()):
+        # t = t0 + evals / R over all runs (least squares)
+        e = np.asarray([x for x, _ in pts], float)
+        t = np.asarray([y for _, y in pts], float)
+        inv_r, t0 = np.polyfit(e, t, 1)
+        print(json.dumps({"fit": "t = t0 + evals / R", "rule": rname, "integrand": fam, "prec": prec,
+                          "t0_us": round(t0 * 1e6, 1), "R_evals_per_s": 1.0 / inv_r if inv_r > 0 else None,
+                          "runs": len(pts)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,7 +445,13 @@ def main():
     ap.add_argument("--prec", default=None, choices=[None, "fp64", "mixed", "ff"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the complexity sweep of Section 6 instead of the benchmark")
+    ap.add_argument("--sweep-budget", default="4e9", help="largest FP64 evaluation count per run")
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
