@@ -13,7 +13,7 @@ LIB = os.path.join(OUT_DIR, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["sg_rules.cpp", "sg_plan.cpp", "sg_kernels.cu", "sg_api.cu", "sg_noalloc.cu"]
-HEADERS = ["sg_internal.h", "sg_kernels.h", "sg_rules.h", "sg_plan.h", "sg_fold_logic.h"]
+HEADERS = ["sg_internal.h", "sg_kernels.h", "sg_rules.h", "sg_plan.h", "sg_fold_logic.h", "sg_reduce.cuh", "sg_ff.cuh"]
 CUDA_INC = "/usr/local/cuda/include"
 
 

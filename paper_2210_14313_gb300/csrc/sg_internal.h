@@ -14,7 +14,9 @@
 //  - a *chunk* is a contiguous range of lexicographic ranks of those
 //    r-subsets: the unit of work stealing.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
+#endif
 
 #define SG_MAX_LEVEL 13       // 1-D rule levels 1..13 (4097 nodes, nested rules)
 #define SG_MAX_L 12           // largest excess level q - d
@@ -117,4 +119,30 @@ struct SgBaseDev {
     double sin_th, cos_th;   // theta_c for the oscillatory kind
     double scale_e2;         // integer power of two of the scale
     double scale_m;          // the scale's remaining factor, in [2^-1/2, 2^1/2]
+};
+
+// Arguments of a fold kernel (the built-in ones and a compiled user integrand's).
+struct SgFoldArgs {
+    const SgItemDev *items;
+    const SgItemVar *vars;           // per item, filled by the setup kernel
+    int nitems;
+    const SgPatDev *pats;
+    const unsigned long long *pat_chunk0;  // per pattern, ascending
+    long long npat;
+    unsigned long long nchunks;
+    const void *tab;                 // float2* or double2*
+    const unsigned long long *binom; // [k][n] table
+    SgSlot *slots;                   // per chunk
+    SgGroupSlot *gslots;             // per reduction group
+    unsigned int *group_done;        // per group chunk tickets (zeroed before launch)
+    unsigned long long *work;        // work-stealing counter (zeroed before launch)
+    unsigned int *item_done;         // per item group tickets (zeroed before launch)
+    const SgBaseDev *bases;          // per integral, for the final assembly
+    const int *item_integral;        // per item: integral index (-1: adjoint sub-sum)
+    SgOutDev *out;                   // per output
+    double *vout;                    // adjoint sub-sum values (per output index)
+    int *flags;                      // guard flags per item (written when guard_tol > 0)
+    const int *skip_unflagged;       // if non-NULL: only items with flags[item] != 0 are run
+    double guard_tol;
+    double unit_roundoff;            // 2^-24 or 2^-53
 };

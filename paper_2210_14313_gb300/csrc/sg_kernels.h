@@ -54,30 +54,7 @@ struct SgSetupArgs {
     double unit_roundoff;
 };
 
-struct SgFoldArgs {
-    const SgItemDev *items;
-    const SgItemVar *vars;           // per item, filled by the prep kernel
-    int nitems;
-    const SgPatDev *pats;
-    const unsigned long long *pat_chunk0;  // per pattern, ascending
-    long long npat;
-    unsigned long long nchunks;
-    const void *tab;                 // float2* or double2*
-    const unsigned long long *binom; // [k][n] table
-    SgSlot *slots;                   // per chunk
-    SgGroupSlot *gslots;             // per reduction group
-    unsigned int *group_done;        // per group chunk tickets (zeroed before launch)
-    unsigned long long *work;        // work-stealing counter (zeroed before launch)
-    unsigned int *item_done;         // per item group tickets (zeroed before launch)
-    const SgBaseDev *bases;          // per integral, for the final assembly
-    const int *item_integral;        // per item: integral index (-1: adjoint sub-sum)
-    SgOutDev *out;                   // per output
-    double *vout;                    // adjoint sub-sum values (per output index)
-    int *flags;                      // guard flags per item (written when guard_tol > 0)
-    const int *skip_unflagged;       // if non-NULL: only items with flags[item] != 0 are run
-    double guard_tol;
-    double unit_roundoff;            // 2^-24 or 2^-53
-};
+
 
 #define SG_APAD 128  // prefix states per warp held in shared memory
 
