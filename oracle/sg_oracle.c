@@ -47,6 +47,11 @@
  *   2 product peak f = prod 1/(a_i^-2 + (x_i - u_i)^2)
  *   3 gaussian     f = exp(-sum a_i^2 (x_i - u_i)^2)
  *   4 gaussian-lin f = exp(-sum a_i (x_i - u_i)^2)
+ * and, for the library's compiled user integrands (test families):
+ *  10 corner peak  f = (1 + sum a_i x_i)^-(d+1)
+ *  11 norm         f = exp(-sqrt(sum a_i (x_i - u_i)^2))
+ *  12 two sums     f = (sum a_i x_i) exp(-sum u_i x_i^2)
+ *  13 polynomial   f = (sum a_i x_i)^3 + (sum u_i x_i)^2
  *
  * Results are returned as (mant, exp2) with Q = mant * 2^exp2, because the
  * product-peak value underflows a double at large d.
@@ -71,6 +76,10 @@
 
 enum { R_TRAP = 1, R_CC = 2, R_GP = 3, R_GL = 4 };
 enum { F_EXPLIN = 0, F_OSC = 1, F_PEAK = 2, F_GAUSS = 3, F_GAUSSLIN = 4 };
+/* Integrands outside the generalised-additive model, for the library's user
+ * integrands (sg_integrand_create): evaluated at every point from the full
+ * d-vector, f(x) - f(c) formed directly. */
+enum { F_UCORNER = 10, F_UNORM = 11, F_UPROD2 = 12, F_UPOLY = 13 };
 enum { FORM_DIFF = 0, FORM_COMB = 1 };
 
 /* ------------------------------------------------------------------------ */
@@ -281,6 +290,33 @@ typedef struct {
     double base;     /* f(c) / scale: 1, or cos(theta_c) */
 } family;
 
+static double general_value(int fam, const double *a, const double *u, int d, const double *x) {
+    double s = 0.0, t = 0.0;
+    switch (fam) {
+    case F_UCORNER:
+        for (int i = 0; i < d; i++) s += a[i] * x[i];
+        return pow(1.0 + s, -(double)(d + 1));
+    case F_UNORM:
+        for (int i = 0; i < d; i++) s += a[i] * (x[i] - u[i]) * (x[i] - u[i]);
+        return exp(-sqrt(s));
+    case F_UPROD2:
+        for (int i = 0; i < d; i++) {
+            s += a[i] * x[i];
+            t += u[i] * x[i] * x[i];
+        }
+        return s * exp(-t);
+    case F_UPOLY:
+        for (int i = 0; i < d; i++) {
+            s += a[i] * x[i];
+            t += u[i] * x[i];
+        }
+        return s * s * s + t * t;
+    }
+    return 0.0;
+}
+
+static int is_general(int fam) { return fam >= F_UCORNER && fam <= F_UPOLY; }
+
 static void family_init(family *F, int fam, const double *params, int d) {
     F->fam = fam;
     F->d = d;
@@ -318,6 +354,11 @@ static void family_init(family *F, int fam, const double *params, int d) {
     }
     F->logscale = s.s;
     F->logscale_lo = s.c;
+    if (is_general(fam)) {  /* scale 1, base f(c) */
+        double c[d > 0 ? d : 1];
+        for (int i = 0; i < d; i++) c[i] = 0.5;
+        F->base = general_value(fam, F->a, F->u, d, c);
+    }
 }
 
 /* (f(x) - f(c)) / scale, evaluated from the full d-vector x. */
@@ -325,6 +366,7 @@ static double family_dev(const family *F, const double *x) {
     const double *a = F->a, *u = F->u;
     int d = F->d;
     double s = 0.0;
+    if (is_general(F->fam)) return general_value(F->fam, a, u, d, x) - F->base;
     switch (F->fam) {
     case F_EXPLIN:
         for (int i = 0; i < d; i++) s += a[i] * (x[i] - 0.5);
@@ -357,6 +399,7 @@ static double family_val(const family *F, const double *x) {
     const double *a = F->a, *u = F->u;
     int d = F->d;
     double s = 0.0;
+    if (is_general(F->fam)) return general_value(F->fam, a, u, d, x);
     switch (F->fam) {
     case F_EXPLIN:
         for (int i = 0; i < d; i++) s += a[i] * x[i];
@@ -540,7 +583,7 @@ static void split_log(double s_hi, double s_lo, double *e0, double *r) {
  */
 int or_integrate(int kind, int fam, const double *params, int d, int L, int form,
                  int nthreads, double *out) {
-    if (!params || !out || fam < 0 || fam > 4) return -1;
+    if (!params || !out || ((fam < 0 || fam > 4) && !is_general(fam))) return -1;
     if (form != FORM_DIFF && form != FORM_COMB) return -1;
     grid G;
     if (grid_init(&G, kind, d, L, form)) return -1;

@@ -483,3 +483,66 @@ def test_gp_difference_form_equals_combination_form(kind):
         b = oracle.integrate(kind, fam, p, 5, 4, oracle.FORM_COMB)
         qa, qb = a.mant * 2.0 ** a.exp2, b.mant * 2.0 ** b.exp2
         assert abs(qa - qb) <= 1e-13 * abs(qb), (kind, fam)
+
+
+# ---------------------------------------------------------------------------
+# Test integrands outside the generalised-additive model (families 10-13),
+# for the library's compiled user integrands
+# ---------------------------------------------------------------------------
+
+def _general_f(fam, p, X):
+    d = X.shape[1]
+    a, u = p[:d], p[d:]
+    if fam == 10:
+        return (1.0 + X @ a) ** (-(d + 1.0))
+    if fam == 11:
+        return np.exp(-np.sqrt(((X - u) ** 2) @ a))
+    if fam == 12:
+        return (X @ a) * np.exp(-((X ** 2) @ u))
+    return (X @ a) ** 3 + (X @ u) ** 2
+
+
+def _general_params(fam, d, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.2, 1.0, d)
+    u = rng.uniform(0.0, 1.0, d)
+    if fam == 10:
+        a = a * (2.0 / a.sum())
+    return np.concatenate([a, u])
+
+
+@pytest.mark.parametrize("fam", [10, 11, 12, 13])
+def test_general_families_match_numpy_on_the_enumerated_grid(fam):
+    # the oracle's point enumeration with f evaluated independently by numpy
+    for kind, d, L in [(CC, 3, 3), (GL, 2, 4), (GP | SLOW, 3, 4)]:
+        p = _general_params(fam, d, 40 + fam + d)
+        for form in (oracle.FORM_DIFF, oracle.FORM_COMB):
+            X, W = oracle.points(kind, d, L, form)
+            ref = float(np.dot(W, _general_f(fam, p, X)))
+            r = oracle.integrate(kind, fam, p, d, L, form)
+            assert abs(r.value - ref) <= 1e-13 * max(1.0, r.cond) * abs(ref), (fam, kind, form)
+
+
+def test_general_polynomial_is_integrated_exactly():
+    # total degree 3 <= 2L + 1 for L >= 1: the Smolyak rule is exact; with
+    # m = sum a / 2 the integral is m^3 + m sum a^2 / 4 + (sum u / 2)^2 + sum u^2 / 12
+    for kind, d, L in [(CC, 5, 1), (GL, 4, 2), (GP | SLOW, 6, 2), (CC, 12, 3)]:
+        p = _general_params(13, d, 90 + d)
+        a, u = p[:d], p[d:]
+        m = a.sum() / 2
+        exact = m ** 3 + m * (a * a).sum() / 4 + (u.sum() / 2) ** 2 + (u * u).sum() / 12
+        r = oracle.integrate(kind, 13, p, d, L)
+        assert abs(r.value - exact) <= 1e-13 * abs(exact), (kind, d, L, r.value, exact)
+
+
+def test_general_corner_peak_converges_to_its_closed_form():
+    # Genz: int (1 + a.x)^-(d+1) = sum_{v in {0,1}^d} (-1)^|v| / (1 + a.v) / (d! prod a)
+    d = 3
+    p = _general_params(10, d, 7)
+    a = p[:d]
+    tot = 0.0
+    for v in itertools.product((0, 1), repeat=d):
+        tot += (-1) ** sum(v) / (1.0 + np.dot(a, v))
+    exact = tot / (math.factorial(d) * np.prod(a))
+    errs = [abs(oracle.integrate(GL, 10, p, d, L).value - exact) / exact for L in (2, 5, 10)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9, errs
