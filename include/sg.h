@@ -42,6 +42,7 @@
 #ifndef SG_H
 #define SG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -232,6 +233,47 @@ SG_API sg_status sg_integrate_batch(const sg_item *items, int n, const double *p
 SG_API sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double *params,
                             int params_on_device, int d, int q, sg_precision prec, void *stream,
                             sg_result *out, double *dparams, int dparams_on_device);
+
+/*
+ * General integrands (the paper's symbolic functions, Section 3, with a
+ * vector state).  A user integrand is CUDA C++ source that defines, for a
+ * state of `state_size` doubles (1..16):
+ *   __device__ void sg_user_centre(double *s, const double *p, int d);
+ *       the state of the centre point c = (1/2, ..., 1/2);
+ *   __device__ void sg_user_move(double *s, int i, double x, const double *p, int d);
+ *       moves direction i (0-based) of the point held in s from 1/2 to x
+ *       (each direction is moved at most once, in increasing order);
+ *   __device__ double sg_user_value(const double *s, const double *p, int d);
+ *       f at the point held in s;
+ * and optionally, after #define SG_USER_DEVIATION,
+ *   __device__ double sg_user_deviation(const double *s, const double *sc,
+ *                                       const double *p, int d);
+ *       f(x) - f(c) for the points held in s and sc, free of cancellation
+ *       (without it the kernel forms sg_user_value(s) - f(c)).
+ * p points to the caller's parameter array.  sg_integrand_create compiles it
+ * with NVRTC for the current device together with the library's fold kernel
+ * (prefix directions moved once per prefix node tuple, one more move and one
+ * evaluation per point).  Errors: SG_EINVAL (NULL, or the source does not
+ * compile: *out is then a handle whose compiler log sg_integrand_log
+ * returns, to be destroyed), SG_ERANGE (state_size), SG_EUNSUPPORTED (no
+ * NVRTC library found), SG_ENOMEM, SG_ECUDA.
+ */
+typedef struct sg_integrand_s *sg_integrand;
+SG_API sg_status sg_integrand_create(const char *source, int state_size, sg_integrand *out);
+SG_API sg_status sg_integrand_destroy(sg_integrand f);
+
+/* Copies the compiler log (NUL-terminated, truncated to cap) and its length. */
+SG_API sg_status sg_integrand_log(sg_integrand f, char *buf, size_t cap, size_t *len);
+
+/*
+ * Q_d^q f for a user integrand f (FP64, telescoped form; host or device
+ * params of nparams >= 0 doubles).  Blocking, like sg_integrate; the result
+ * is Q = f(c) + sum_p W_p (f(x_p) - f(c)) with the same fields.  Errors as
+ * sg_integrate; SG_EINVAL also for a handle that failed to compile or was
+ * compiled for another device.
+ */
+SG_API sg_status sg_integrate_user(sg_rule rule, sg_integrand f, const double *params, int nparams,
+                                   int params_on_device, int d, int q, void *stream, sg_result *out);
 
 /* Static description of a status code. */
 SG_API const char *sg_status_string(sg_status s);

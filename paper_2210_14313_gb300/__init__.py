@@ -34,7 +34,8 @@ ABI_SYMBOLS = ["sg_rule_init", "sg_rule_init_growth", "sg_rule_destroy", "sg_rul
                "sg_integrate", "sg_integrate_async", "sg_integrate_batch", "sg_integrate_grad",
                "sg_status_string", "sg_get_tuning", "sg_set_tuning", "sg_autotune",
                "sg_profile_begin", "sg_profile_end", "sg_ceiling", "sg_integrate_noalloc",
-               "sg_eval_functions"]
+               "sg_eval_functions", "sg_integrand_create", "sg_integrand_destroy", "sg_integrand_log",
+               "sg_integrate_user"]
 
 
 class SgError(RuntimeError):
@@ -100,6 +101,10 @@ def load(build_if_missing: bool = True):
     lib.sg_ceiling.argtypes = [ip, ip, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sg_integrate_noalloc.argtypes = [ip, ip, vp, ip, ip, ip, vp, vp]
     lib.sg_eval_functions.argtypes = [ip, ip, vp, vp, ip, vp]
+    lib.sg_integrand_create.argtypes = [ctypes.c_char_p, ip, ctypes.POINTER(vp)]
+    lib.sg_integrand_destroy.argtypes = [vp]
+    lib.sg_integrand_log.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    lib.sg_integrate_user.argtypes = [vp, vp, vp, ip, ip, ip, ip, vp, ctypes.POINTER(sg_result)]
     for name in ABI_SYMBOLS:
         if name != "sg_status_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -265,6 +270,69 @@ def integrate_batch(specs, pool, prec: int = PREC_MIXED, guard_tol: float = 0.0,
                                      _stream_handle(stream), res), "sg_integrate_batch")
     del keep
     return [Result(r) for r in res]
+
+
+class Integrand:
+    """A user integrand compiled at run time (sg_integrand_create): CUDA C++
+    source defining sg_user_centre / sg_user_move / sg_user_value (and
+    optionally sg_user_deviation) over a state of ``state_size`` doubles."""
+
+    def __init__(self, source: str, state_size: int):
+        _require_cuda()
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.sg_integrand_create(source.encode(), state_size, ctypes.byref(h))
+        if st != 0:
+            log = _integrand_log(h) if h.value else ""
+            if h.value:
+                lib.sg_integrand_destroy(h)
+            err = SgError(st, "sg_integrand_create")
+            err.log = log
+            raise err
+        self.handle = h
+        self.state_size = state_size
+
+    def log(self) -> str:
+        return _integrand_log(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sg_integrand_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _integrand_log(h) -> str:
+    lib = load()
+    n = ctypes.c_size_t(0)
+    lib.sg_integrand_log(h, None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    lib.sg_integrand_log(h, buf, n.value + 1, None)
+    return buf.value.decode(errors="replace")
+
+
+def integrate_user(rule: Rule, f: Integrand, params, d: int, q: int, stream=None) -> Result:
+    """Q_d^q of a user integrand (FP64); params: host or CUDA array of doubles."""
+    lib = load()
+    if params is None:
+        params = np.zeros(0)
+    if isinstance(params, np.ndarray) or not hasattr(params, "data_ptr"):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        ptr, n, on_dev = p.ctypes.data_as(ctypes.c_void_p), p.size, 0
+    else:
+        import torch
+        if params.dtype != torch.float64 or not params.is_contiguous():
+            raise ValueError("params must be a contiguous float64 tensor")
+        ptr, n, on_dev = ctypes.c_void_p(params.data_ptr()), params.numel(), 1
+    r = sg_result()
+    _check(lib.sg_integrate_user(rule.handle, f.handle, ptr, n, on_dev, d, q, _stream_handle(stream),
+                                 ctypes.byref(r)), "sg_integrate_user")
+    return Result(r)
 
 
 def integrate_grad(rule: Rule, fam: int, params, d: int, q: int, prec: int = PREC_FP64, stream=None):

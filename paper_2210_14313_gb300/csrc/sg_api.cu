@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/sg.h"
+#include "sg_user.h"
 #include "sg_kernels.h"
 #include "sg_plan.h"
 #include "sg_rules.h"
@@ -508,8 +509,49 @@ static SgLaunchCfg fold_cfg(const Plan *P, int prec, DevCtx *C) {
 
 // Enqueues the whole computation of a plan on W->stream (capturable: no
 // allocation, no synchronisation).  prec_run: 0 FP64, 1 mixed.
+// A user integrand's compiled fold kernel and what it is launched with.
+struct UserFold {
+    cudaKernel_t kern;
+    int K;
+    const double *params;
+    int d;
+};
+
+// Host image of SgUserArgs in sg_user_kernel.cuh (same layout).
+struct SgUserArgsHost {
+    const double *params;
+    int d;
+    int pad;
+};
+
+static cudaError_t launch_user_fold(const UserFold &uf, SgFoldArgs &fa, const Plan *P, DevCtx *C,
+                                    cudaStream_t s) {
+    const int warps = 4;
+    const size_t smem = (size_t)warps * (SG_USER_APAD * (uf.K + 1) * sizeof(double) + SG_MAX_R * sizeof(int));
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)uf.kern, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, 8));
+    long long ctas = (long long)C->sms * per_sm;
+    const long long need = (long long)((P->nchunks + warps - 1) / warps);
+    if (need < ctas) ctas = std::max<long long>(need, 1);
+    SgUserArgsHost ua{uf.params, uf.d, 0};
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)ctas);
+    lc.blockDim = dim3(32 * warps);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = P->nchunks <= SG_DEPENDENT_LAUNCH_MAX_CHUNKS ? 1 : 0;
+    void *args[] = {&fa, &ua};
+    return cudaLaunchKernelExC(&lc, (const void *)uf.kern, args);
+}
+
 static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *d_params,
-                          double guard_tol, SgOutDev *d_out, cudaStream_t s) {
+                          double guard_tol, SgOutDev *d_out, cudaStream_t s, const UserFold *uf = nullptr) {
     const int prec = P->prec;
     const int nitems = (int)P->items.size();
     SgOutDev *outp = d_out ? d_out : (SgOutDev *)W->out.p;
@@ -574,7 +616,8 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     fa.guard_tol = guard_tol;
     fa.unit_roundoff = u;
     CK(prof_mark(W, true, s));
-    CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
+    if (uf) CK(launch_user_fold(*uf, fa, P, C, s));
+    else CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
     CK(prof_mark(W, false, s));
     if (prec == 1 && guard_tol > 0.0) {
         // precision guard: recompute flagged items in float-float
@@ -703,6 +746,51 @@ extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *par
     }
     CK(cudaEventRecord(W->ev0, s));
     ST(run_plan(P, W, C, dp, 0.0, nullptr, s));
+    CK(cudaEventRecord(W->ev1, s));
+    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, W->ev0, W->ev1);
+    fill_result(*(SgOutDev *)W->h_pinned, P, 0, ms, out);
+    return SG_OK;
+}
+
+extern "C" sg_status sg_integrate_user(sg_rule rule, sg_integrand f, const double *params, int nparams,
+                                       int params_on_device, int d, int q, void *stream, sg_result *out) {
+    if (!rule || !out || nparams < 0 || (nparams > 0 && !params)) return SG_EINVAL;
+    UserFold uf;
+    int fdev = 0;
+    if (!sg_integrand_kernel(f, &uf.kern, &uf.K, &fdev)) return SG_EINVAL;
+    if (d < 1 || q < d) return SG_EINVAL;
+    if (d > SG_MAX_D) return SG_ERANGE;
+    if (q - d > SG_MAX_L || q - d + 1 > rule->max_level) return SG_ERANGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SG_ECUDA;
+    if (dev != rule->device || dev != fdev) return SG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Plan *P = nullptr;
+    std::vector<Req> reqs(1);
+    memset(reqs.data(), 0, sizeof(Req));
+    reqs[0] = Req{rule, SG_FAM_USER, d, q - d, (int)SG_FORM_TELESCOPED, 0, 0};
+    ST(get_plan(reqs, SG_PREC_FP64, &P));
+    Workspace *W = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    ST(get_ws(s, &W));
+    ST(ws_prepare(W, P, false, true, false, params_on_device ? 0 : std::max<size_t>(1, (size_t)nparams)));
+    ST(ensure_host(W, sizeof(SgOutDev)));
+    const double *dp = params;
+    if (!params_on_device) {
+        if (nparams > 0)
+            CK(cudaMemcpyAsync(W->params.p, params, (size_t)nparams * sizeof(double), cudaMemcpyHostToDevice, s));
+        dp = (const double *)W->params.p;
+    }
+    uf.params = dp;
+    uf.d = d;
+    CK(cudaEventRecord(W->ev0, s));
+    ST(run_plan(P, W, C, dp, 0.0, nullptr, s, &uf));
     CK(cudaEventRecord(W->ev1, s));
     CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

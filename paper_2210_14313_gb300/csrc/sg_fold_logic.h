@@ -196,3 +196,25 @@ SG_HD void sg_chunk_span(const SgPatDev *P, unsigned long long c, unsigned long 
         *a_hi = *a_lo + P->ablk < P->A ? *a_lo + P->ablk : P->A;
     }
 }
+
+#if defined(__CUDACC__)
+// Lexicographic unranking of the chunk's first r-subset by the whole warp:
+// each round tests 32 candidates of one position at once (sg_unrank_*), so
+// a position costs one or two rounds of parallel table loads instead of a
+// serial binary search.  Lane 0 writes the subset to idx.
+__device__ __forceinline__ void unrank_warp(unsigned long long rank, int d, int r,
+                                            const unsigned long long *B, int *idx, int lane) {
+    int p = -1;
+    for (int t = 0; t < r; t++) {
+        SgUnrankPos u;
+        sg_unrank_begin(&u, rank, d, r, t, p, B);
+        for (;;) {
+            const unsigned m = __ballot_sync(0xffffffffu, sg_unrank_test(&u, sg_unrank_candidate(&u, lane), d, B));
+            if (sg_unrank_narrow(&u, m)) break;
+        }
+        rank -= u.total - sg_binom(B, d - u.lo, u.k);
+        if (lane == 0) idx[t] = u.lo;
+        p = u.lo;
+    }
+}
+#endif

@@ -24,6 +24,10 @@
 #define SG_MAX_D 8192         // largest dimension
 #define SG_BINOM_K (SG_MAX_R + 2)
 
+// Family of a user integrand compiled at run time (sg_integrand_create): its
+// tables hold the node coordinates x instead of phi_i(x).
+#define SG_FAM_USER 5
+
 // Integrand deviation kinds evaluated per point (the "G" of the kernels).
 #define SG_GK_EXPM1 0  // D = expm1(S)                 (exp-linear, gaussian(s), product peak)
 #define SG_GK_OSC 1    // D = cos(phi + S) - cos(phi)   (oscillatory)

@@ -395,26 +395,6 @@ __device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long
     F.habs = habs;
 }
 
-// Lexicographic unranking of the chunk's first r-subset by the whole warp:
-// each round tests 32 candidates of one position at once (sg_unrank_*), so
-// a position costs one or two rounds of parallel table loads instead of a
-// serial binary search.  Lane 0 writes the subset to idx.
-__device__ __forceinline__ void unrank_warp(unsigned long long rank, int d, int r,
-                                            const unsigned long long *B, int *idx, int lane) {
-    int p = -1;
-    for (int t = 0; t < r; t++) {
-        SgUnrankPos u;
-        sg_unrank_begin(&u, rank, d, r, t, p, B);
-        for (;;) {
-            const unsigned m = __ballot_sync(FULL_MASK, sg_unrank_test(&u, sg_unrank_candidate(&u, lane), d, B));
-            if (sg_unrank_narrow(&u, m)) break;
-        }
-        rank -= u.total - sg_binom(B, d - u.lo, u.k);
-        if (lane == 0) idx[t] = u.lo;
-        p = u.lo;
-    }
-}
-
 template <typename T, int GK>
 __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                            const SgItemDev *__restrict__ I, unsigned long long c,
@@ -590,7 +570,8 @@ __global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
         const SgIntegralDev G = A.integrals[g];
         const double *a = A.params + G.param_off, *u = a + G.d;
         double s = 0.0, c = 0.0;
-        for (int i = lane; i < G.d; i += 32) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
+        if (G.fam != SG_FAM_USER)  // a user integrand's parameters have no fixed layout
+            for (int i = lane; i < G.d; i += 32) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
         // combine the lanes' compensated pairs by a fixed butterfly (the same
         // order on every call; five dependent steps instead of 32)
         for (int o = 1; o < 32; o <<= 1) {
@@ -666,7 +647,7 @@ __global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
         const int i = (int)(local / B.m), j = (int)(local - (long long)i * B.m);
         const double2 xw = B.xw[j];
         const double *p = A.params + G.param_off;
-        const double phi = phi_table(G.fam, p[i], p[G.d + i], xw.x);
+        const double phi = G.fam == SG_FAM_USER ? xw.x : phi_table(G.fam, p[i], p[G.d + i], xw.x);
         if (A.tab64) A.tab64[B.off + local] = make_double2(phi, xw.y);
         if (A.tab32) A.tab32[B.off + local] = make_float2((float)phi, (float)xw.y);
         if (A.tabff) {

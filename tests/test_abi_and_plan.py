@@ -143,3 +143,47 @@ def test_library_growth_matches_oracle(kind):
                 order, order_o = np.argsort(xb, kind="stable"), np.argsort(xo, kind="stable")
                 assert np.allclose(xb[order], xo[order_o], rtol=0, atol=4e-16)
                 assert np.allclose(wb[order], wo[order_o], rtol=0, atol=1e-14 * np.abs(wo).max())
+
+
+def _nvrtc():
+    import ctypes
+    for name in ("libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            pass
+    pytest.skip("NVRTC not available")
+
+
+def _nvrtc_compile(lib, source, k):
+    # the program sg_integrand_create builds: user source + the library's fold
+    # kernel, with its headers given to NVRTC by name
+    import ctypes
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2210_14313_gb300", "csrc")
+    names = ["sg_internal.h", "sg_fold_logic.h", "sg_reduce.cuh", "sg_user_kernel.cuh"]
+    hdrs = [open(os.path.join(csrc, n)).read().encode() for n in names]
+    prog = ctypes.c_void_p()
+    src = (source + '\n#include "sg_user_kernel.cuh"\n').encode()
+    assert lib.nvrtcCreateProgram(ctypes.byref(prog), src, b"sg_user.cu", 4, (ctypes.c_char_p * 4)(*hdrs),
+                                  (ctypes.c_char_p * 4)(*[n.encode() for n in names])) == 0
+    opts = [b"--gpu-architecture=sm_103", ("-DSG_USER_K=%d" % k).encode(), b"-std=c++17", b"-default-device"]
+    rc = lib.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    n = ctypes.c_size_t()
+    lib.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    lib.nvrtcGetProgramLog(prog, buf)
+    lib.nvrtcDestroyProgram(ctypes.byref(prog))
+    return rc, buf.value.decode(errors="replace")
+
+
+def test_user_integrand_programs_compile():
+    import user_integrands as ui
+    lib = _nvrtc()
+    for name, (src, k, _) in ui.CASES.items():
+        rc, log = _nvrtc_compile(lib, src, k)
+        assert rc == 0, (name, log)
+    rc, log = _nvrtc_compile(lib, ui.EXPLIN, 2)
+    assert rc == 0, log
+    rc, log = _nvrtc_compile(lib, ui.BROKEN, 1)
+    assert rc != 0 and "undefined_name" in log
