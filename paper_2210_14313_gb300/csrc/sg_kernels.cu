@@ -126,8 +126,8 @@ __device__ __forceinline__ float sg_expm1f(float x) {
 // r^15 and of cos to r^16 leave truncation errors below 7e-17 relative and
 // 3e-18 absolute.  The quadrant swaps and sign flips are integer operations
 // on the result words.  Arguments below pi/4 skip the reduction: 17 FP64
-// instructions, 22 with it.  GB300's FP64 unit is charged per active lane,
-// so lanes taking different branches cost no FP64 time.
+// instructions, 22 with it (in the fold most lanes of a warp agree on this
+// branch; a split warp runs both paths with fewer active lanes each).
 __device__ __noinline__ double2 sg_sincos_slow(double x) {
     double s, c;
     sincos(x, &s, &c);
@@ -184,8 +184,8 @@ __device__ __forceinline__ void sg_sincos_d(double x, double *sp, double *cp) {
 }
 
 // expm1 in double for the fold, with the number of Taylor terms chosen by
-// the argument's size (GB300 charges FP64 work per active lane, so the
-// branches cost no FP64 time):
+// the argument's size (the exponential workloads' arguments are uniformly
+// small, so the lanes of a warp take the same branch):
 //   |x| < 2^-5:  x + x^2 (1/2! + ... + x^6/8!), remainder below 3e-18 rel.;
 //   |x| < ln2/2: the series to x^14/14!, remainder below 3e-19 rel.;
 //   |x| < 700:   Cody & Waite reduction x = k ln2 + r with ln 2 in two parts
@@ -362,7 +362,8 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
         F.hc = hc;
         F.habs = habs;
     } else {
-        // FP64 (charged per active lane): the flat layout
+        // FP64: the flat layout (idle lanes at the end of a run cost the FP64
+        // pipe nothing on GB300; the lane groups measured no faster)
         SgFlatPos f(lane, E);
         double acc = F.acc;
         for (; f.a < At; f.step()) {
