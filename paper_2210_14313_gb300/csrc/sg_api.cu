@@ -590,7 +590,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     sa.vout = (double *)W->vout.p;
     sa.unit_roundoff = u;
     CK(sg_launch_setup(sa, s));
-    if (P->nchunks == 0) return SG_OK;
+    if (P->nchunks == 0 && !uf) return SG_OK;  // a user fold also writes the centre-only result
     SgFoldArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.items = P->d_items;

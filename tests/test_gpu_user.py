@@ -91,3 +91,13 @@ def test_compile_error_is_reported():
     with pytest.raises(sg.SgError) as e:
         sg.Integrand(ui.BROKEN, 1)
     assert "undefined_name" in e.value.log
+
+
+def test_user_centre_only_rule(integrands, rules):
+    # q = d: the Smolyak rule is the centre point with weight 1
+    d = 7
+    p = _params(12, d, 3)
+    r = sg.integrate_user(rules["cc"], integrands["two_sums"], p, d, d)
+    a, u = p[:d], p[d:]
+    assert r.value == pytest.approx(0.5 * a.sum() * math.exp(-0.25 * u.sum()), rel=1e-15)
+    assert r.points == 1
