@@ -122,12 +122,14 @@ __device__ __forceinline__ float sg_expm1f(float x) {
 // x = k pi/2 + r with pi/2 in three parts, the first two of 33 significant
 // bits so that k * part is exact for |k| < 2^20; k is rounded by adding
 // 1.5 * 2^52 to x * 2/pi, whose low word then holds k mod 2^32 (the
-// quadrant).  On |r| <= pi/4 (plus rounding) the Taylor series of sin to
-// r^15 and of cos to r^16 leave truncation errors below 7e-17 relative and
-// 3e-18 absolute.  The quadrant swaps and sign flips are integer operations
-// on the result words.  Arguments below pi/4 skip the reduction: 17 FP64
-// instructions, 22 with it (in the fold most lanes of a warp agree on this
-// branch; a split warp runs both paths with fewer active lanes each).
+// quadrant).  On |r| <= 0.7854 (pi/4 plus rounding) sin r = r + r^3 S(r^2)
+// and cos r = 1 - r^2/2 + r^4 C(r^2) with S and C of degree 5, minimax fits
+// of the relative error (Remez exchange, gen_poly.py): 1.1e-17 and 1.1e-18
+// relative with the coefficients rounded to doubles.  The quadrant swaps and
+// sign flips are integer operations on the result words.  Arguments below
+// pi/4 skip the reduction: 15 FP64 instructions, 20 with it (in the fold
+// most lanes of a warp agree on this branch; a split warp runs both paths
+// with fewer active lanes each).
 __device__ __noinline__ double2 sg_sincos_slow(double x) {
     double s, c;
     sincos(x, &s, &c);
@@ -158,24 +160,22 @@ __device__ __forceinline__ void sg_sincos_d(double x, double *sp, double *cp) {
         r = fma(-k, 2.02226624879595063540e-21, r);  // tail
     }
     const double z = r * r;
-    // sin r = r + r z (-1/3! + z (1/5! - z (1/7! - ... - z/15!)))
-    double ps = -7.64716373181981647590e-13;          // -1/15!
-    ps = fma(ps, z, 1.60590438368216145994e-10);      //  1/13!
-    ps = fma(ps, z, -2.50521083854417187751e-08);     // -1/11!
-    ps = fma(ps, z, 2.75573192239858906526e-06);      //  1/9!
-    ps = fma(ps, z, -1.98412698412698412526e-04);     // -1/7!
-    ps = fma(ps, z, 8.33333333333333321769e-03);      //  1/5!
-    ps = fma(ps, z, -1.66666666666666657415e-01);     // -1/3!
+    // sin r = r + r z S(z)
+    double ps = 1.5896229413316947e-10;
+    ps = fma(ps, z, -2.505074775041537e-08);
+    ps = fma(ps, z, 2.7557313621308956e-06);
+    ps = fma(ps, z, -0.00019841269829589325);
+    ps = fma(ps, z, 0.008333333333322118);
+    ps = fma(ps, z, -0.1666666666666663);
     const double sr = fma(r * z, ps, r);
-    // cos r = 1 + z (-1/2! + z (1/4! - z (1/6! - ... + z/16!)))
-    double pc = 4.77947733238738529744e-14;           //  1/16!
-    pc = fma(pc, z, -1.14707455977297247139e-11);     // -1/14!
-    pc = fma(pc, z, 2.08767569878680989792e-09);      //  1/12!
-    pc = fma(pc, z, -2.75573192239858906526e-07);     // -1/10!
-    pc = fma(pc, z, 2.48015873015873015873e-05);      //  1/8!
-    pc = fma(pc, z, -1.38888888888888894189e-03);     // -1/6!
-    pc = fma(pc, z, 4.16666666666666643537e-02);      //  1/4!
-    pc = fma(pc, z, -0.5);                            // -1/2!
+    // cos r = 1 + z (-1/2 + z C(z))
+    double pc = -1.1358536026755315e-11;
+    pc = fma(pc, z, 2.0875700832666822e-09);
+    pc = fma(pc, z, -2.755731417923013e-07);
+    pc = fma(pc, z, 2.480158728885148e-05);
+    pc = fma(pc, z, -0.0013888888888873056);
+    pc = fma(pc, z, 0.041666666666666595);
+    pc = fma(pc, z, -0.5);
     const double cr = fma(z, pc, 1.0);
     // x = k pi/2 + r: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s) for k mod 4
     const double a = (q & 1u) ? cr : sr, b = (q & 1u) ? sr : cr;
@@ -183,48 +183,48 @@ __device__ __forceinline__ void sg_sincos_d(double x, double *sp, double *cp) {
     *cp = sg_flip_sign(b, ((q + 1u) & 2u) << 30);
 }
 
-// expm1 in double for the fold, with the number of Taylor terms chosen by
-// the argument's size (the exponential workloads' arguments are uniformly
-// small, so the lanes of a warp take the same branch):
-//   |x| < 2^-5:  x + x^2 (1/2! + ... + x^6/8!), remainder below 3e-18 rel.;
-//   |x| < ln2/2: the series to x^14/14!, remainder below 3e-19 rel.;
+// expm1 in double for the fold, with the polynomial's length chosen by the
+// argument's size (the exponential workloads' arguments are uniformly small,
+// so the lanes of a warp take the same branch):
+//   |x| < 2^-5:  x + x^2 P5(x), P5 of degree 5, 1.2e-17 relative;
+//   |x| < ln2/2: x + x^2 P10(x), P10 of degree 10, 9e-19 relative;
 //   |x| < 700:   Cody & Waite reduction x = k ln2 + r with ln 2 in two parts
 //                (head of 32 bits: k * head exact), k rounded by adding
-//                1.5 * 2^52, the series of expm1(r) to r^14, and
+//                1.5 * 2^52, expm1(r) by P10, and
 //                expm1(x) = 2^k expm1(r) + (2^k - 1) with 2^k from integer bits;
 //   otherwise (overflow, -1, Inf, NaN): the library expm1 out of line.
+// P5 and P10 are minimax fits of the relative error of expm1 (Remez
+// exchange, gen_poly.py), the errors above with the coefficients rounded to
+// doubles.
 __device__ __noinline__ double sg_expm1_slow(double x) { return expm1(x); }
 
-// the series of expm1 from x^2/2! to x^14/14!, times 1/x^2
-__device__ __forceinline__ double sg_expm1_p14(double x) {
-    double p = 1.1470745597729725e-11;        // 1/14!
-    p = fma(p, x, 1.6059043836821613e-10);    // 1/13!
-    p = fma(p, x, 2.08767569878681e-09);      // 1/12!
-    p = fma(p, x, 2.505210838544172e-08);     // 1/11!
-    p = fma(p, x, 2.755731922398589e-07);     // 1/10!
-    p = fma(p, x, 2.7557319223985893e-06);    // 1/9!
-    p = fma(p, x, 2.48015873015873e-05);      // 1/8!
-    p = fma(p, x, 0.0001984126984126984);     // 1/7!
-    p = fma(p, x, 0.001388888888888889);      // 1/6!
-    p = fma(p, x, 0.008333333333333333);      // 1/5!
-    p = fma(p, x, 0.041666666666666664);      // 1/4!
-    p = fma(p, x, 0.16666666666666666);       // 1/3!
-    return fma(p, x, 0.5);                    // 1/2!
+// P10 of expm1(x) = x + x^2 P10(x) on |x| <= ln2/2
+__device__ __forceinline__ double sg_expm1_p10(double x) {
+    double p = 2.087532890649324e-09;
+    p = fma(p, x, 2.5108967892867137e-08);
+    p = fma(p, x, 2.7557402614361874e-07);
+    p = fma(p, x, 2.755724440308346e-06);
+    p = fma(p, x, 2.4801587172609534e-05);
+    p = fma(p, x, 0.00019841269885940077);
+    p = fma(p, x, 0.0013888888888962316);
+    p = fma(p, x, 0.0083333333333217);
+    p = fma(p, x, 0.04166666666666651);
+    p = fma(p, x, 0.16666666666666677);
+    return fma(p, x, 0.5);
 }
 
 __device__ __forceinline__ double sg_expm1_d(double x) {
     const int hx = __double2hiint(x) & 0x7fffffff;
     if (hx < 0x3fa00000) {  // |x| < 2^-5
-        double p = 2.48015873015873e-05;      // 1/8!
-        p = fma(p, x, 0.0001984126984126984); // 1/7!
-        p = fma(p, x, 0.001388888888888889);  // 1/6!
-        p = fma(p, x, 0.008333333333333333);  // 1/5!
-        p = fma(p, x, 0.041666666666666664);  // 1/4!
-        p = fma(p, x, 0.16666666666666666);   // 1/3!
-        p = fma(p, x, 0.5);                   // 1/2!
+        double p = 0.00019841315662246908;
+        p = fma(p, x, 0.0013889312449012385);
+        p = fma(p, x, 0.008333333336939659);
+        p = fma(p, x, 0.04166666664601192);
+        p = fma(p, x, 0.1666666666666651);
+        p = fma(p, x, 0.5000000000000026);
         return fma(x * x, p, x);
     }
-    if (hx < 0x3fd62e42) return fma(x * x, sg_expm1_p14(x), x);  // |x| < 0.34657...
+    if (hx < 0x3fd62e42) return fma(x * x, sg_expm1_p10(x), x);  // |x| < 0.34657...
     if (hx >= 0x4085e000) return sg_expm1_slow(x);               // |x| >= 700, Inf, NaN
     const double magic = 6755399441055744.0;  // 1.5 * 2^52
     const double t = fma(x, 1.4426950408889634, magic);
@@ -232,7 +232,7 @@ __device__ __forceinline__ double sg_expm1_d(double x) {
     const double kd = t - magic;
     double r = fma(-kd, 6.9314718060195446e-01, x);  // ln 2 head (32 bits)
     r = fma(-kd, -4.2009150726810846e-11, r);         // tail
-    const double p = fma(r * r, sg_expm1_p14(r), r);  // expm1(r)
+    const double p = fma(r * r, sg_expm1_p10(r), r);  // expm1(r)
     const double scale = __hiloint2double((k + 1023) << 20, 0);
     return fma(scale, p, scale - 1.0);
 }
