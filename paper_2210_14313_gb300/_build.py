@@ -17,7 +17,7 @@ SOURCES = ["sg_rules.cpp", "sg_plan.cpp", "sg_kernels.cu", "sg_api.cu", "sg_noal
 EMBEDDED = [("sg_src_internal", "sg_internal.h"), ("sg_src_fold_logic", "sg_fold_logic.h"),
             ("sg_src_reduce", "sg_reduce.cuh"), ("sg_src_user_kernel", "sg_user_kernel.cuh")]
 HEADERS = ["sg_internal.h", "sg_kernels.h", "sg_rules.h", "sg_plan.h", "sg_fold_logic.h", "sg_reduce.cuh",
-           "sg_ff.cuh", "sg_user.h", "sg_user_kernel.cuh"]
+           "sg_ff.cuh", "sg_user.h", "sg_user_kernel.cuh", "sg_fixed.h"]
 CUDA_INC = "/usr/local/cuda/include"
 
 

@@ -1,18 +1,16 @@
-"""Coefficients of the fold's double-precision sin, cos and expm1 polynomials
-(sg_kernels.cu): weighted minimax fits by the Remez exchange algorithm
+"""Coefficients of the FP64 fold's sin, cos and expm1 polynomials
+(sg_fixed.h): weighted minimax fits by the Remez exchange algorithm
 (Remez 1934; as in Cheney, Introduction to Approximation Theory, ch. 3),
-computed in 60-digit arithmetic with mpmath and rounded to the nearest double.
+computed in 60-digit arithmetic with mpmath and rounded to 0.64 fixed point.
 
     sin r  = r + r^3 S(r^2),          S of degree 5,  |r| <= 0.7854
     cos r  = 1 - r^2/2 + r^4 C(r^2),  C of degree 5,  |r| <= 0.7854
     expm1 x = x + x^2 P(x),           P of degree 10, |x| <= ln2/2
-                                      P of degree 5,  |x| <= 2^-5
 
 Each fit minimises the relative error of the function itself (the weight is
 the factor that turns the polynomial's error into it).  Run as a script to
-print the coefficients (highest degree first, as the kernels' Horner loops
-take them) and each rounded polynomial's largest relative error on a dense
-grid, evaluated exactly.
+print the coefficient magnitudes with their signs and each polynomial's
+largest relative error on a dense grid, evaluated exactly.
 """
 import mpmath as mp
 
@@ -92,27 +90,32 @@ FITS = {
     "sin": (_sin_t, _sin_w, (mp.mpf(0), RHO ** 2), 5),
     "cos": (_cos_t, _cos_w, (mp.mpf(0), RHO ** 2), 5),
     "expm1": (_expm1_t, _expm1_w, (-H, H), 10),
-    "expm1_small": (_expm1_t, _expm1_w, (-mp.mpf(2) ** -5, mp.mpf(2) ** -5), 5),
 }
 
 
-def coefficients(name):
-    """The fit's coefficients rounded to doubles, lowest degree first."""
+def fixed_coefficients(name):
+    """The fit's coefficient magnitudes in unsigned 0.64 fixed point
+    (round(|c| 2^64)) and their signs, lowest degree first: the integer
+    evaluation (sg_fixed.h) works on magnitudes."""
     f, w, (a, b), n = FITS[name]
-    return [float(x) for x in remez(f, w, a, b, n)]
+    c = remez(f, w, a, b, n)
+    return [int(mp.nint(abs(x) * mp.mpf(2) ** 64)) for x in c], [1 if x > 0 else -1 for x in c]
 
 
-def rounded_error(name, coef, N=4000):
-    """Largest relative error of the rounded polynomial (exact evaluation)."""
+def fixed_error(name, N=4000):
+    """Largest relative error of the polynomial with the fixed-point
+    coefficients, evaluated exactly, on a grid of N + 1 points."""
     f, w, (a, b), _ = FITS[name]
-    cm = [mp.mpf(x) for x in coef]
+    mags, signs = fixed_coefficients(name)
+    cm = [sg * mp.mpf(m) / mp.mpf(2) ** 64 for m, sg in zip(mags, signs)]
     return max(abs(w(x) * (f(x) - mp.polyval(cm[::-1], x)))
                for x in (a + (b - a) * mp.mpf(k) / N for k in range(N + 1)))
 
 
 if __name__ == "__main__":
     for name in FITS:
-        coef = coefficients(name)
-        print("%s: rounded polynomial's max relative error %.3g" % (name, float(rounded_error(name, coef))))
-        for c in coef[::-1]:
-            print("    %r" % c)
+        mags, signs = fixed_coefficients(name)
+        print("%s: largest relative error %.3g; 0.64 magnitudes, lowest degree first:"
+              % (name, float(fixed_error(name))))
+        for m, sg in zip(mags, signs):
+            print("    %s%dull" % ("+" if sg > 0 else "-", m))

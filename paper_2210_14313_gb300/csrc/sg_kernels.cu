@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "sg_ff.cuh"
+#include "sg_fixed.h"
 #include "sg_fold_logic.h"
 #include "sg_kernels.h"
 #include "sg_reduce.cuh"
@@ -122,14 +123,11 @@ __device__ __forceinline__ float sg_expm1f(float x) {
 // x = k pi/2 + r with pi/2 in three parts, the first two of 33 significant
 // bits so that k * part is exact for |k| < 2^20; k is rounded by adding
 // 1.5 * 2^52 to x * 2/pi, whose low word then holds k mod 2^32 (the
-// quadrant).  On |r| <= 0.7854 (pi/4 plus rounding) sin r = r + r^3 S(r^2)
-// and cos r = 1 - r^2/2 + r^4 C(r^2) with S and C of degree 5, minimax fits
-// of the relative error (Remez exchange, gen_poly.py): 1.1e-17 and 1.1e-18
-// relative with the coefficients rounded to doubles.  The quadrant swaps and
-// sign flips are integer operations on the result words.  Arguments below
-// pi/4 skip the reduction: 15 FP64 instructions, 20 with it (in the fold
-// most lanes of a warp agree on this branch; a split warp runs both paths
-// with fewer active lanes each).
+// quadrant).  On |r| <= 0.7854 (pi/4 plus rounding) sin r and cos r come from
+// the fixed-point polynomials of sg_fixed.h.  The quadrant swaps and sign
+// flips are integer operations on the result words.  Arguments below pi/4
+// skip the reduction (in the fold most lanes of a warp agree on this
+// branch).
 __device__ __noinline__ double2 sg_sincos_slow(double x) {
     double s, c;
     sincos(x, &s, &c);
@@ -142,108 +140,58 @@ __device__ __forceinline__ double sg_flip_sign(double v, unsigned m) {
 
 __device__ __forceinline__ void sg_sincos_d(double x, double *sp, double *cp) {
     const int hx = __double2hiint(x) & 0x7fffffff;
-    double r = x;
-    unsigned q = 0;
-    if (hx >= 0x3fe921fb) {  // |x| >= 0.7853979... (just below pi/4): reduce
-        if (hx >= 0x41300000) {  // |x| >= 2^20, Inf, NaN
-            const double2 v = sg_sincos_slow(x);
-            *sp = v.x;
-            *cp = v.y;
-            return;
-        }
-        const double magic = 6755399441055744.0;  // 1.5 * 2^52
-        const double t = fma(x, 6.36619772367581382433e-01, magic);
-        q = (unsigned)__double2loint(t);
-        const double k = t - magic;
-        r = fma(-k, 1.57079632673412561417e+00, x);  // pi/2 head (33 bits)
-        r = fma(-k, 6.07710050630396597660e-11, r);  // middle (33 bits)
-        r = fma(-k, 2.02226624879595063540e-21, r);  // tail
+    if (hx < 0x3fe921fb) {  // |x| < 0.7853975... (just below pi/4)
+        sg_fx_sincos(x, sp, cp);
+        return;
     }
-    const double z = r * r;
-    // sin r = r + r z S(z)
-    double ps = 1.5896229413316947e-10;
-    ps = fma(ps, z, -2.505074775041537e-08);
-    ps = fma(ps, z, 2.7557313621308956e-06);
-    ps = fma(ps, z, -0.00019841269829589325);
-    ps = fma(ps, z, 0.008333333333322118);
-    ps = fma(ps, z, -0.1666666666666663);
-    const double sr = fma(r * z, ps, r);
-    // cos r = 1 + z (-1/2 + z C(z))
-    double pc = -1.1358536026755315e-11;
-    pc = fma(pc, z, 2.0875700832666822e-09);
-    pc = fma(pc, z, -2.755731417923013e-07);
-    pc = fma(pc, z, 2.480158728885148e-05);
-    pc = fma(pc, z, -0.0013888888888873056);
-    pc = fma(pc, z, 0.041666666666666595);
-    pc = fma(pc, z, -0.5);
-    const double cr = fma(z, pc, 1.0);
+    if (hx >= 0x41300000) {  // |x| >= 2^20, Inf, NaN
+        const double2 v = sg_sincos_slow(x);
+        *sp = v.x;
+        *cp = v.y;
+        return;
+    }
+    const double magic = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, 6.36619772367581382433e-01, magic);
+    const unsigned q = (unsigned)__double2loint(t);
+    const double k = t - magic;
+    double r = fma(-k, 1.57079632673412561417e+00, x);  // pi/2 head (33 bits)
+    r = fma(-k, 6.07710050630396597660e-11, r);         // middle (33 bits)
+    r = fma(-k, 2.02226624879595063540e-21, r);         // tail
+    double sr, cr;
+    sg_fx_sincos(r, &sr, &cr);
     // x = k pi/2 + r: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s) for k mod 4
     const double a = (q & 1u) ? cr : sr, b = (q & 1u) ? sr : cr;
     *sp = sg_flip_sign(a, (q & 2u) << 30);
     *cp = sg_flip_sign(b, ((q + 1u) & 2u) << 30);
 }
 
-// expm1 in double for the fold, with the polynomial's length chosen by the
-// argument's size (the exponential workloads' arguments are uniformly small,
-// so the lanes of a warp take the same branch):
-//   |x| < 2^-5:  x + x^2 P5(x), P5 of degree 5, 1.2e-17 relative;
-//   |x| < ln2/2: x + x^2 P10(x), P10 of degree 10, 9e-19 relative;
+// expm1 in double for the fold:
+//   |x| < ln2/2: the fixed-point polynomial of sg_fixed.h;
 //   |x| < 700:   Cody & Waite reduction x = k ln2 + r with ln 2 in two parts
 //                (head of 32 bits: k * head exact), k rounded by adding
-//                1.5 * 2^52, expm1(r) by P10, and
+//                1.5 * 2^52, expm1(r) as above, and
 //                expm1(x) = 2^k expm1(r) + (2^k - 1) with 2^k from integer bits;
 //   otherwise (overflow, -1, Inf, NaN): the library expm1 out of line.
-// P5 and P10 are minimax fits of the relative error of expm1 (Remez
-// exchange, gen_poly.py), the errors above with the coefficients rounded to
-// doubles.
 __device__ __noinline__ double sg_expm1_slow(double x) { return expm1(x); }
-
-// P10 of expm1(x) = x + x^2 P10(x) on |x| <= ln2/2
-__device__ __forceinline__ double sg_expm1_p10(double x) {
-    double p = 2.087532890649324e-09;
-    p = fma(p, x, 2.5108967892867137e-08);
-    p = fma(p, x, 2.7557402614361874e-07);
-    p = fma(p, x, 2.755724440308346e-06);
-    p = fma(p, x, 2.4801587172609534e-05);
-    p = fma(p, x, 0.00019841269885940077);
-    p = fma(p, x, 0.0013888888888962316);
-    p = fma(p, x, 0.0083333333333217);
-    p = fma(p, x, 0.04166666666666651);
-    p = fma(p, x, 0.16666666666666677);
-    return fma(p, x, 0.5);
-}
 
 __device__ __forceinline__ double sg_expm1_d(double x) {
     const int hx = __double2hiint(x) & 0x7fffffff;
-    if (hx < 0x3fa00000) {  // |x| < 2^-5
-        double p = 0.00019841315662246908;
-        p = fma(p, x, 0.0013889312449012385);
-        p = fma(p, x, 0.008333333336939659);
-        p = fma(p, x, 0.04166666664601192);
-        p = fma(p, x, 0.1666666666666651);
-        p = fma(p, x, 0.5000000000000026);
-        return fma(x * x, p, x);
-    }
-    if (hx < 0x3fd62e42) return fma(x * x, sg_expm1_p10(x), x);  // |x| < 0.34657...
-    if (hx >= 0x4085e000) return sg_expm1_slow(x);               // |x| >= 700, Inf, NaN
+    if (hx < 0x3fd62e42) return sg_fx_expm1(x);   // |x| < 0.34657...
+    if (hx >= 0x4085e000) return sg_expm1_slow(x);  // |x| >= 700, Inf, NaN
     const double magic = 6755399441055744.0;  // 1.5 * 2^52
     const double t = fma(x, 1.4426950408889634, magic);
     const int k = __double2loint(t);
     const double kd = t - magic;
     double r = fma(-kd, 6.9314718060195446e-01, x);  // ln 2 head (32 bits)
     r = fma(-kd, -4.2009150726810846e-11, r);         // tail
-    const double p = fma(r * r, sg_expm1_p10(r), r);  // expm1(r)
     const double scale = __hiloint2double((k + 1023) << 20, 0);
-    return fma(scale, p, scale - 1.0);
+    return fma(scale, sg_fx_expm1(r), scale - 1.0);
 }
 
 // Per-point deviation (the "G" evaluation).
 template <typename T, int GK> __device__ __forceinline__ T gdev(T S, T sphi, T cphi);
 template <> __device__ __forceinline__ float gdev<float, SG_GK_EXPM1>(float S, float, float) {
     return sg_expm1f(S);
-}
-template <> __device__ __forceinline__ double gdev<double, SG_GK_EXPM1>(double S, double, double) {
-    return sg_expm1_d(S);
 }
 // Oscillatory: H is half the folded phase deviation; returns
 // sin(H) sin(phi + H), and the factor -2 of
@@ -253,10 +201,20 @@ template <> __device__ __forceinline__ float gdev<float, SG_GK_OSC>(float H, flo
     sincosf(H, &sh, &ch);
     return sh * fmaf(sphi, ch, cphi * sh);
 }
-template <> __device__ __forceinline__ double gdev<double, SG_GK_OSC>(double H, double sphi, double cphi) {
-    double sh, ch;
-    sg_sincos_d(H, &sh, &ch);
-    return sh * fma(sphi, ch, cphi * sh);
+
+// The FP64 deviation: expm1 of the folded argument, or for the oscillatory
+// kind sin(H) sin(phi + H) (factor -2 in the weights), in fixed point below
+// |H| = pi/4 and through the reduced sin and cos above it.
+template <int GK>
+__device__ __forceinline__ double gdev_d(double S, double sphi, double cphi, const SgFxPhase &ph) {
+    if constexpr (GK == SG_GK_EXPM1) {
+        return sg_expm1_d(S);
+    } else {
+        if ((__double2hiint(S) & 0x7fffffff) < 0x3fe921fb) return sg_fx_osc_dev(S, ph);
+        double sh, ch;
+        sg_sincos_d(S, &sh, &ch);
+        return sh * fma(sphi, ch, cphi * sh);
+    }
 }
 
 // Float-float deviation (see sg_ff.cuh): expm1, or for the oscillatory kind
@@ -366,10 +324,11 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
         // pipe nothing on GB300; the lane groups measured no faster)
         SgFlatPos f(lane, E);
         double acc = F.acc;
+        const SgFxPhase ph = sg_fx_phase(sphi, cphi);
         for (; f.a < At; f.step()) {
             const double2 p = sP[f.a];
             const V2 te = tail_entry(tab, base1, E1, base2, f.e);
-            acc = fma(p.y * te.y, gdev<double, GK>(p.x + te.x, sphi, cphi), acc);
+            acc = fma(p.y * te.y, gdev_d<GK>(p.x + te.x, sphi, cphi, ph), acc);
         }
         F.acc = acc;
     }
@@ -818,6 +777,7 @@ __global__ void __launch_bounds__(256) sg_ceiling_kernel(int sweeps, double *out
     }
     T S = (T)(blockIdx.x * 1e-6), W = (T)0.7;
     const T sphi = (T)0.3, cphi = (T)0.95;
+    const SgFxPhase ph = sg_fx_phase(0.3, 0.95);
     double acc = 0.0, aabs = 0.0;
     float hs = 0.f, hc = 0.f, habs = 0.f;
     for (int it = 0; it < sweeps; it++) {
@@ -836,7 +796,7 @@ __global__ void __launch_bounds__(256) sg_ceiling_kernel(int sweeps, double *out
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 const double s = S + dl[k], w = W * wl[k];
-                const double D = gdev<double, GK>(s, sphi, cphi);
+                const double D = gdev_d<GK>(s, sphi, cphi, ph);
                 acc = fma(w, D, acc);
                 aabs = fma(fabs(w), fabs(D), aabs);
             }

@@ -76,3 +76,15 @@ def block(kind, bk, k):
     dp = ctypes.POINTER(ctypes.c_double)
     n = lib.chk_block(kind, bk, k, x.ctypes.data_as(dp), w.ctypes.data_as(dp))
     return x[:n].copy(), w[:n].copy()
+
+
+def fixed(kind, x, phi=0.0):
+    """The FP64 fold's fixed-point functions built for the host (sg_fixed.h):
+    kind 0 expm1, kind 1 (sin, cos) pairs, kind 2 sin(x) sin(phi + x)."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_fixed.argtypes = [ctypes.c_int, dp, dp, ctypes.c_longlong, ctypes.c_double]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(len(x) * (2 if kind == 1 else 1))
+    lib.chk_fixed(kind, x.ctypes.data_as(dp), y.ctypes.data_as(dp), len(x), phi)
+    return y

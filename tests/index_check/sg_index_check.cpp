@@ -15,6 +15,7 @@
 
 #include <vector>
 
+#include "../../paper_2210_14313_gb300/csrc/sg_fixed.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_fold_logic.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_plan.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_rules.h"
@@ -342,4 +343,22 @@ long long chk_unrank(int d, int r, long long n) {
 // The library's level rule and blocks, built on the host (no device needed).
 int chk_rule(int kind, int level, double *x, double *w) { return sg_rule_level(kind, level, x, w); }
 int chk_block(int kind, int bk, int k, double *x, double *w) { return sg_block(kind, bk, k, x, w); }
+
+// The fixed-point elementary functions of the FP64 fold (sg_fixed.h), built
+// for the host: kind 0: expm1(x) for |x| <= ln2/2;
+// kind 1: sin and cos for |x| <= 0.7854 (y holds pairs); kind 2:
+// sin(x) sin(phi + x) with phi = params[0].
+void chk_fixed(int kind, const double *x, double *y, long long n, double phi) {
+    const SgFxPhase ph = sg_fx_phase(sin(phi), cos(phi));
+    for (long long i = 0; i < n; i++) {
+        if (kind == 0) {
+            y[i] = sg_fx_expm1(x[i]);
+        } else if (kind == 1) {
+            sg_fx_sincos(x[i], &y[2 * i], &y[2 * i + 1]);
+        } else {
+            y[i] = sg_fx_osc_dev(x[i], ph);
+        }
+    }
 }
+
+}  // extern "C"

@@ -1,4 +1,4 @@
-"""The fold's double sin, cos and expm1 polynomials (sg_kernels.cu) are the
+"""The FP64 fold's sin, cos and expm1 polynomials (sg_fixed.h) are the
 minimax fits that gen_poly.py computes, and those fits meet their error
 bounds against mpmath's functions."""
 import os
@@ -12,15 +12,19 @@ CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2210_14313_gb300", "
 sys.path.insert(0, CSRC)
 import gen_poly  # noqa: E402
 
-BOUNDS = {"sin": 2e-17, "cos": 2e-18, "expm1": 2e-18, "expm1_small": 2e-17}
+BOUNDS = {"sin": 1e-17, "cos": 1e-18, "expm1": 1e-18}
+PREFIX = {"sin": "SG_FX_SIN", "cos": "SG_FX_COS", "expm1": "SG_FX_EXP"}
+# the sign patterns the integer Horner loops of sg_fixed.h are written for
+SIGNS = {"sin": [-1, 1] * 3, "cos": [1, -1] * 3, "expm1": [1] * 11}
 
 
 @pytest.mark.parametrize("name", sorted(BOUNDS))
-def test_kernel_coefficients_are_the_minimax_fit(name):
-    with open(os.path.join(CSRC, "sg_kernels.cu")) as f:
+def test_fixed_coefficients_are_the_minimax_fit(name):
+    with open(os.path.join(CSRC, "sg_fixed.h")) as f:
         src = f.read()
-    coef = gen_poly.coefficients(name)
-    missing = [c for c in coef if repr(c) not in src and c != 0.5]
-    assert not missing, (name, missing)
-    err = gen_poly.rounded_error(name, coef, N=1500)
+    mags, signs = gen_poly.fixed_coefficients(name)
+    assert signs == SIGNS[name]
+    for k, m in enumerate(mags):
+        assert "#define %s%d %dull" % (PREFIX[name], k, m) in src, (name, k, m)
+    err = gen_poly.fixed_error(name, N=1500)
     assert err <= BOUNDS[name], (name, float(err))
