@@ -15,9 +15,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sg_rules.cpp", "sg_plan.cpp", "sg_kernels.cu", "sg_api.cu", "sg_noalloc.cu", "sg_user.cu"]
 # sources compiled at run time for user integrands, embedded into the library as strings
 EMBEDDED = [("sg_src_internal", "sg_internal.h"), ("sg_src_fold_logic", "sg_fold_logic.h"),
-            ("sg_src_reduce", "sg_reduce.cuh"), ("sg_src_user_kernel", "sg_user_kernel.cuh")]
+            ("sg_src_xsum", "sg_xsum.h"), ("sg_src_reduce", "sg_reduce.cuh"),
+            ("sg_src_user_kernel", "sg_user_kernel.cuh")]
 HEADERS = ["sg_internal.h", "sg_kernels.h", "sg_rules.h", "sg_plan.h", "sg_fold_logic.h", "sg_reduce.cuh",
-           "sg_ff.cuh", "sg_user.h", "sg_user_kernel.cuh", "sg_fixed.h"]
+           "sg_ff.cuh", "sg_user.h", "sg_user_kernel.cuh", "sg_fixed.h", "sg_xsum.h"]
 CUDA_INC = "/usr/local/cuda/include"
 
 

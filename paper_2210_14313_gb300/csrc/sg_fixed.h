@@ -87,6 +87,35 @@ SG_FX double sg_fx_to_double(sg_u64 v, sg_u64 neg, int q) {
     return sg_fx_from_bits((v ? b : 0ull) | (neg << 63));
 }
 
+// as sg_fx_to_double, for any q: results below the normal range are flushed
+// to zero
+SG_FX double sg_fx_to_double_f(sg_u64 v, sg_u64 neg, int q) {
+    const int n = sg_fx_clz(v) & 63;
+    const sg_u64 m = v << n;
+    const sg_u64 sig = (m >> 11) + ((m >> 10) & 1ull);
+    const int ef = 1085 - n - q;  // biased exponent less one
+    const sg_u64 b = ((sg_u64)ef << 52) + sig;
+    return sg_fx_from_bits((v != 0 && ef >= 0 ? b : 0ull) | (neg << 63));
+}
+
+// A double as |x| = m 2^(e - 1086) with m its significand shifted to bit 63
+// (the leading one at bit 63 for normal numbers) and e its biased exponent
+// (1 for subnormals); neg is its sign bit.
+struct SgFxNorm {
+    sg_u64 m, neg;
+    int e;
+};
+
+SG_FX SgFxNorm sg_fx_norm(double x) {
+    const sg_u64 b = sg_fx_bits(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    SgFxNorm r;
+    r.m = ((b & 0xfffffffffffffull) | ((sg_u64)(e != 0) << 52)) << 11;
+    r.e = e != 0 ? e : 1;
+    r.neg = b >> 63;
+    return r;
+}
+
 // sin r = r + r^3 S(r^2), S = sum s_k z^k, signs -, +, -, +, -, +
 #define SG_FX_SIN0 3074457345618251973ull
 #define SG_FX_SIN1 153722867280706050ull
@@ -161,32 +190,44 @@ SG_FX SgFxPhase sg_fx_phase(double s, double c) {
     return p;
 }
 
-// sin(H) sin(phi + H) for |H| <= 0.7854, as H B with
-// B = (sin H / H) (sin phi cos H + cos phi sin H) in fixed point.  The
-// absolute error is a few units of |H| 2^-61: within 2 ulp of the result
-// unless |sin(phi + H)| is small, where it stays far below the rounding
-// error of the same expression evaluated in FP64.
-SG_FX double sg_fx_osc_dev(double H, const SgFxPhase &ph) {
-    const sg_u64 a = sg_fx_fix(H, 64);
+// For a = |H| in 0.64, |H| <= 0.7854, and H's sign mask nh: the magnitude of
+// B = (sin H / H) (sin phi cos H + cos phi sin H) in 3.61, and its sign mask
+SG_FX sg_u64 sg_fx_osc_b(sg_u64 a, sg_u64 nh, const SgFxPhase &ph, sg_u64 *nb) {
     sg_u64 w, kc;
     sg_fx_sincos_k(a, &w, &kc);
     const sg_u64 ks = (1ull << 63) - (w >> 1);                  // sin H / H, 1.63
-    const sg_u64 nh = (sg_u64)((long long)sg_fx_bits(H) >> 63);
     const sg_u64 t1 = sg_fx_mulhi(ph.ms, kc);                   // |sin phi| cos H, 2.62
     const sg_u64 t2 = sg_fx_mulhi(ph.mc, sg_fx_mulhi(a, ks));   // |cos phi| |sin H|, 2.62
     const sg_u64 n2 = ph.nc ^ nh;
     const sg_u64 u = ((t1 ^ ph.ns) - ph.ns) + ((t2 ^ n2) - n2);  // sin(phi + H), signed 2.62
-    const sg_u64 nu = (sg_u64)((long long)u >> 63);
-    const sg_u64 b = sg_fx_mulhi((u ^ nu) - nu, ks);            // |B|, 3.61
-    return H * sg_fx_to_double(b, nu & 1ull, 61);
+    *nb = (sg_u64)((long long)u >> 63);
+    return sg_fx_mulhi((u ^ *nb) - *nb, ks);
 }
 
-// expm1(x) for |x| <= ln2/2 (about 0.3466) as x + x (x P(x)), one rounding
-// after the fixed-point part.  All coefficients are positive, so the Horner
-// sums P_k = p_k +- |x| P_{k+1} stay positive.
-SG_FX double sg_fx_expm1(double x) {
-    const sg_u64 a = sg_fx_fix(x, 64);
-    const sg_u64 n = (sg_u64)((long long)sg_fx_bits(x) >> 63);
+// sin(H) sin(phi + H) for |H| <= 0.7854, as H B.  The absolute error is a few
+// units of |H| 2^-61: within 2 ulp of the result unless |sin(phi + H)| is
+// small, where it stays far below the rounding error of the same expression
+// evaluated in FP64.
+SG_FX double sg_fx_osc_dev(double H, const SgFxPhase &ph) {
+    sg_u64 nb;
+    const sg_u64 b = sg_fx_osc_b(sg_fx_fix(H, 64), (sg_u64)((long long)sg_fx_bits(H) >> 63), ph, &nb);
+    return H * sg_fx_to_double(b, nb & 1ull, 61);
+}
+
+// w sin(H) sin(phi + H) for |H| <= 0.7854: the product H B w formed from B
+// and the normalised significands of H and w, rounded once
+SG_FX double sg_fx_osc_dev_w(double H, double w, const SgFxPhase &ph) {
+    const SgFxNorm h = sg_fx_norm(H), g = sg_fx_norm(w);
+    sg_u64 nb;
+    const sg_u64 b = sg_fx_osc_b(sg_fx_fix(H, 64), 0ull - h.neg, ph, &nb);
+    const sg_u64 v = sg_fx_mulhi(sg_fx_mulhi(b, h.m), g.m);  // |H B w| 2^(2105 - eH - ew)
+    return sg_fx_to_double_f(v, (nb ^ h.neg ^ g.neg) & 1ull, 2105 - h.e - g.e);
+}
+
+// P(x) of expm1(x) = x + x^2 P(x) in 0.64, for a = |x| in 0.64, |x| <= ln2/2
+// (about 0.3466), and x's sign mask n.  All coefficients are positive, so
+// the Horner sums P_k = p_k +- |x| P_{k+1} stay positive.
+SG_FX sg_u64 sg_fx_expm1_p(sg_u64 a, sg_u64 n) {
     sg_u64 p = SG_FX_EXP10;
     p = SG_FX_EXP9 + ((sg_fx_mulhi(a, p) ^ n) - n);
     p = SG_FX_EXP8 + ((sg_fx_mulhi(a, p) ^ n) - n);
@@ -197,6 +238,24 @@ SG_FX double sg_fx_expm1(double x) {
     p = SG_FX_EXP3 + ((sg_fx_mulhi(a, p) ^ n) - n);
     p = SG_FX_EXP2 + ((sg_fx_mulhi(a, p) ^ n) - n);
     p = SG_FX_EXP1 + ((sg_fx_mulhi(a, p) ^ n) - n);
-    p = SG_FX_EXP0 + ((sg_fx_mulhi(a, p) ^ n) - n);    // P(x), 0.64
-    return fma(x, sg_fx_to_double(sg_fx_mulhi(a, p), n & 1ull, 64), x);
+    return SG_FX_EXP0 + ((sg_fx_mulhi(a, p) ^ n) - n);
+}
+
+// expm1(x) for |x| <= ln2/2 as x + x (x P(x)), one rounding after the
+// fixed-point part
+SG_FX double sg_fx_expm1(double x) {
+    const sg_u64 a = sg_fx_fix(x, 64);
+    const sg_u64 n = (sg_u64)((long long)sg_fx_bits(x) >> 63);
+    return fma(x, sg_fx_to_double(sg_fx_mulhi(a, sg_fx_expm1_p(a, n)), n & 1ull, 64), x);
+}
+
+// w expm1(x) for |x| <= ln2/2: the product x (1 + x P(x)) w formed from the
+// normalised significands of x and w, rounded once
+SG_FX double sg_fx_expm1_w(double x, double w) {
+    const SgFxNorm h = sg_fx_norm(x), g = sg_fx_norm(w);
+    const sg_u64 a = sg_fx_fix(x, 64), n = 0ull - h.neg;
+    const sg_u64 t = sg_fx_mulhi(a, sg_fx_expm1_p(a, n)) >> 2;  // |x| P(x), 2.62
+    const sg_u64 k = (1ull << 62) + ((t ^ n) - n);               // 1 + x P(x), 2.62
+    const sg_u64 v = sg_fx_mulhi(sg_fx_mulhi(k, h.m), g.m);       // |x k w| 2^(2106 - ex - ew)
+    return sg_fx_to_double_f(v, (h.neg ^ g.neg) & 1ull, 2106 - h.e - g.e);
 }

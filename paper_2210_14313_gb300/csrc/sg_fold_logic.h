@@ -166,6 +166,40 @@ struct SgLaneGroups {
     }
 };
 
+// Division by a block size without a divide instruction: for 0 <= q < 2^31
+// and 1 <= m < 2^31, with l = ceil(log2 m) and M = floor(2^(31 + l) / m) + 1
+// (< 2^32), q / m = floor(q M / 2^(31 + l)) (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", 1994, Thm. 4.2).
+struct SgDivMagic {
+    unsigned M;
+    int sh;
+};
+
+SG_HD SgDivMagic sg_div_magic(int m) {
+#ifdef __CUDA_ARCH__
+    const int l = m > 1 ? 32 - __clz(m - 1) : 0;
+#else
+    int l = 0;
+    while ((1ll << l) < (long long)m) l++;
+#endif
+    SgDivMagic g;
+    g.M = (unsigned)((1ull << (31 + l)) / (unsigned long long)m + 1ull);
+    g.sh = 31 + l;
+    return g;
+}
+
+SG_HD int sg_div_magic_q(int q, SgDivMagic g) {
+    return (int)(((unsigned long long)(unsigned)q * g.M) >> g.sh);
+}
+
+// One prefix position of the current run: the table row of its direction,
+// its block size m and m's division magic.
+struct SgPrefixPos {
+    long long row;
+    SgDivMagic dm;
+    int m, pad;
+};
+
 // Table entry of prefix position t for prefix node tuple q (mixed radix over
 // the prefix block sizes, the last prefix position fastest).  Returns the
 // entry offset relative to the item's table and leaves q / m in *q.

@@ -202,18 +202,25 @@ template <> __device__ __forceinline__ float gdev<float, SG_GK_OSC>(float H, flo
     return sh * fmaf(sphi, ch, cphi * sh);
 }
 
-// The FP64 deviation: expm1 of the folded argument, or for the oscillatory
-// kind sin(H) sin(phi + H) (factor -2 in the weights), in fixed point below
-// |H| = pi/4 and through the reduced sin and cos above it.
+// The FP64 deviation times a tail weight w: w expm1(S), or for the
+// oscillatory kind w sin(H) sin(phi + H) (factor -2 in the prefix weights),
+// in fixed point (one rounding) on |S| < ln2/2 and |H| < pi/4, through the
+// double functions above otherwise.
 template <int GK>
-__device__ __forceinline__ double gdev_d(double S, double sphi, double cphi, const SgFxPhase &ph) {
+__device__ __forceinline__ double gdevw_d(double S, double w, double sphi, double cphi, const SgFxPhase &ph) {
+    const int hx = __double2hiint(S) & 0x7fffffff;
     if constexpr (GK == SG_GK_EXPM1) {
-        return sg_expm1_d(S);
+        double v = sg_fx_expm1_w(S, w);
+        if (hx >= 0x3fd62e42) v = sg_expm1_d(S) * w;
+        return v;
     } else {
-        if ((__double2hiint(S) & 0x7fffffff) < 0x3fe921fb) return sg_fx_osc_dev(S, ph);
-        double sh, ch;
-        sg_sincos_d(S, &sh, &ch);
-        return sh * fma(sphi, ch, cphi * sh);
+        double v = sg_fx_osc_dev_w(S, w, ph);
+        if (hx >= 0x3fe921fb) {
+            double sh, ch;
+            sg_sincos_d(S, &sh, &ch);
+            v = sh * fma(sphi, ch, cphi * sh) * w;
+        }
+        return v;
     }
 }
 
@@ -328,7 +335,7 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
         for (; f.a < At; f.step()) {
             const double2 p = sP[f.a];
             const V2 te = tail_entry(tab, base1, E1, base2, f.e);
-            acc = fma(p.y * te.y, gdev_d<GK>(p.x + te.x, sphi, cphi, ph), acc);
+            acc = fma(p.y, gdevw_d<GK>(p.x + te.x, te.y, sphi, cphi, ph), acc);
         }
         F.acc = acc;
     }
@@ -358,7 +365,8 @@ __device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long
 template <typename T, int GK>
 __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                            const SgItemDev *__restrict__ I, unsigned long long c,
-                           typename PrefixState<T>::type *sP, int *sIdx, int lane, FoldAcc &F,
+                           typename PrefixState<T>::type *sP, SgPrefixPos *sPos, int *sIdx, int lane,
+                           FoldAcc &F,
                            bool &waited) {
     typedef typename V2T<T>::type V2;
     const V2 *__restrict__ tab = (const V2 *)A.tab + I->tab;
@@ -375,6 +383,12 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
         cudaGridDependencySynchronize();
         waited = true;
     }
+    // the prefix positions' block sizes and their division magics (per chunk)
+    if (lane < r - 1) {
+        const int m = P->pm[lane];
+        sPos[lane].m = m;
+        sPos[lane].dm = sg_div_magic(m);
+    }
     __syncwarp();
     const SgItemVar *V = A.vars + (I - A.items);
     typedef typename std::conditional<std::is_same<T, FFTag>::value, float, T>::type TS;
@@ -384,15 +398,22 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
         const int plast = sIdx[r - 1];
         const int run = (unsigned long long)(d - plast) < cnt ? d - plast : (int)cnt;
         const SgTailSegs seg = sg_tail_segments(P->toff, tm, plast, run, skip);
+        // this run's table rows of the prefix directions
+        if (lane < r - 1) sPos[lane].row = P->poff[lane] + (long long)sg_actual_dir(sIdx[lane], skip) * sPos[lane].m;
+        __syncwarp();
         for (int ab = a_lo; ab < a_hi; ab += SG_APAD) {
             const int At = a_hi - ab < SG_APAD ? a_hi - ab : SG_APAD;
-            // fold the prefix directions: one state per prefix node tuple
+            // fold the prefix directions: one state per prefix node tuple (its
+            // digits in the mixed radix of the block sizes, the last fastest)
             for (int a = lane; a < At; a += 32) {
                 int q = ab + a;
                 if constexpr (std::is_same<T, FFTag>::value) {  // float-float
                     ff2 S = {0.f, 0.f}, W = {(float)gdev_weight<GK>(), 0.f};
                     for (int t = r - 2; t >= 0; t--) {
-                        const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
+                        const SgPrefixPos pp = sPos[t];
+                        const int qn = sg_div_magic_q(q, pp.dm);
+                        const V2 e = tab[pp.row + (q - qn * pp.m)];
+                        q = qn;
                         S = ff_add(S, ff2{e.x, e.y});
                         W = ff_mul(W, ff2{e.z, e.w});
                     }
@@ -400,7 +421,10 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                 } else {
                     T S = 0, W = (T)gdev_weight<GK>();
                     for (int t = r - 2; t >= 0; t--) {
-                        const V2 e = tab[sg_prefix_entry(P, t, sg_actual_dir(sIdx[t], skip), &q)];
+                        const SgPrefixPos pp = sPos[t];
+                        const int qn = sg_div_magic_q(q, pp.dm);
+                        const V2 e = tab[pp.row + (q - qn * pp.m)];
+                        q = qn;
                         S += e.x;
                         W *= e.y;
                     }
@@ -429,7 +453,8 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     PS *sP = (PS *)smem + (size_t)warp * SG_APAD;
-    int *sIdx = (int *)(smem + (size_t)nw * SG_APAD * sizeof(PS)) + warp * SG_MAX_R;
+    SgPrefixPos *sPos = (SgPrefixPos *)(smem + (size_t)nw * SG_APAD * sizeof(PS)) + warp * SG_MAX_R;
+    int *sIdx = (int *)(smem + (size_t)nw * (SG_APAD * sizeof(PS) + SG_MAX_R * sizeof(SgPrefixPos))) + warp * SG_MAX_R;
     bool waited = false;
     for (;;) {
         unsigned long long c = 0;
@@ -448,21 +473,17 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         if (A.skip_unflagged && !A.flags[item]) continue;
         const SgItemDev *I = A.items + item;
         FoldAcc F;
-        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sIdx, lane, F, waited);
-        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sIdx, lane, F, waited);
+        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+        // the chunk's sum over the lanes, exact before one rounding
         double acc, aabs;
         if constexpr (std::is_same<T, double>::value) {
             // the FP64 fold skips |W D| per point: the chunk's |sum| stands in
-            acc = F.acc;
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+            acc = warp_sum(F.acc);
             aabs = fabs(acc);
         } else {
-            acc = std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa);
-            aabs = (double)F.habs;
-            for (int o = 16; o > 0; o >>= 1) {
-                acc += __shfl_xor_sync(FULL_MASK, acc, o);
-                aabs += __shfl_xor_sync(FULL_MASK, aabs, o);
-            }
+            acc = warp_sum(std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa));
+            aabs = warp_sum((double)F.habs);
         }
         if (lane == 0) {
             SgSlot sl;
@@ -502,8 +523,8 @@ __device__ __forceinline__ SgItemVar item_values(const SgItemRole &R, const SgIn
     }
     if (G.fam == 1) {
         // phase theta + shift: rotate (sin, cos) by the shift
-        double ss, cc;
-        sincos(shift, &ss, &cc);
+        double ss = 0.0, cc = 1.0;
+        if (shift != 0.0) sincos(shift, &ss, &cc);
         V.sin_phi = sn * cc + cs * ss;
         V.cos_phi = cs * cc - sn * ss;
         V.base_rel = V.cos_phi;
@@ -512,65 +533,84 @@ __device__ __forceinline__ SgItemVar item_values(const SgItemRole &R, const SgIn
         V.sin_phi = 0.0;
         V.cos_phi = 1.0;
         V.base_rel = 1.0;
-        V.mult = exp(shift);
+        V.mult = shift != 0.0 ? exp(shift) : 1.0;
     }
     return V;
 }
 
-// Blocks [0, nbase) compute one integral per warp: log f(c) as a compensated
-// sum in a fixed order (lane-strided Neumaier, lanes combined in order), or
-// the oscillatory centre phase.  The remaining blocks fill table entries.
-__global__ void sg_setup_kernel(SgSetupArgs A, int nbase) {
+// Blocks [0, nbase) compute one integral each: log f(c) as a compensated sum
+// in a fixed order (thread-strided Neumaier sums, combined by fixed trees
+// within and across the block's warps), or the oscillatory centre phase.  A
+// whole block per integral spreads a long sum over the SM's four FP64
+// units.  The remaining blocks fill table entries.
+__global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase) {
     // let a fold launched as a programmatic dependent start its plan-only work
     cudaTriggerProgrammaticLaunchCompletion();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((int)blockIdx.x < nbase) {
-        const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        if (g >= A.nintegrals) return;
+        __shared__ double sh_s[8], sh_c[8];
+        __shared__ SgBaseDev sh_b;
+        const int g = blockIdx.x;
         const SgIntegralDev G = A.integrals[g];
         const double *a = A.params + G.param_off, *u = a + G.d;
         double s = 0.0, c = 0.0;
         if (G.fam != SG_FAM_USER)  // a user integrand's parameters have no fixed layout
-            for (int i = lane; i < G.d; i += 32) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
-        // combine the lanes' compensated pairs by a fixed butterfly (the same
-        // order on every call; five dependent steps instead of 32)
+            for (int i = threadIdx.x; i < G.d; i += blockDim.x) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
+        // combine compensated pairs by a fixed tree: at level o the lower lane
+        // of each pair adds the upper one's pair.  GB300 runs FP64 at a rate
+        // per active lane, so the steps, and the scalar work below, run on
+        // the lanes that need them only.
         for (int o = 1; o < 32; o <<= 1) {
-            const double so = __shfl_xor_sync(FULL_MASK, s, o), co = __shfl_xor_sync(FULL_MASK, c, o);
-            // lower lane of each pair first, so both lanes compute the same sum
-            double s1 = (lane & o) ? so : s, c1 = (lane & o) ? co : c;
-            double s2 = (lane & o) ? s : so, c2 = (lane & o) ? c : co;
-            neu_add(s1, c1, s2);
-            c1 += c2;
-            s = s1;
-            c = c1;
+            const double so = __shfl_down_sync(FULL_MASK, s, o), co = __shfl_down_sync(FULL_MASK, c, o);
+            if ((lane & (2 * o - 1)) == 0) {
+                neu_add(s, c, so);
+                c += co;
+            }
         }
-        const double S = s, C = c;
-        SgBaseDev B;
-        if (G.fam == 1) {
-            B.log_hi = 0.0;
-            B.log_lo = 0.0;
-            sincos(6.28318530717958647693 * u[0] + (S + C), &B.sin_th, &B.cos_th);
-            B.base = B.cos_th;
-        } else {
-            B.log_hi = S;
-            B.log_lo = C;
-            B.base = 1.0;
-            B.sin_th = 0.0;
-            B.cos_th = 1.0;
+        if (lane == 0) {
+            sh_s[warp] = s;
+            sh_c[warp] = c;
         }
-        // exp(log_hi + log_lo) = 2^e0 exp(r), r = log_hi - e0 ln 2 + log_lo with ln 2
-        // split in two (Cody & Waite): the result's scale without overflow
-        {
-            const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-            const double e0 = floor(B.log_hi * 1.44269504088896338700);
-            const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
-            B.scale_e2 = e0;
-            B.scale_m = exp(rr);
+        __syncthreads();
+        if (warp == 0) {
+            s = lane < nw ? sh_s[lane] : 0.0;
+            c = lane < nw ? sh_c[lane] : 0.0;
+            for (int o = 1; o < nw; o <<= 1) {
+                const double so = __shfl_down_sync(FULL_MASK, s, o), co = __shfl_down_sync(FULL_MASK, c, o);
+                if ((lane & (2 * o - 1)) == 0) {
+                    neu_add(s, c, so);
+                    c += co;
+                }
+            }
+            if (lane == 0) {
+                SgBaseDev B;
+                if (G.fam == 1) {
+                    B.log_hi = 0.0;
+                    B.log_lo = 0.0;
+                    sg_sincos_d(6.28318530717958647693 * u[0] + (s + c), &B.sin_th, &B.cos_th);
+                    B.base = B.cos_th;
+                } else {
+                    B.log_hi = s;
+                    B.log_lo = c;
+                    B.base = 1.0;
+                    B.sin_th = 0.0;
+                    B.cos_th = 1.0;
+                }
+                // exp(log_hi + log_lo) = 2^e0 exp(r), r = log_hi - e0 ln 2 + log_lo with
+                // ln 2 split in two (Cody & Waite): the result's scale without overflow
+                const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+                const double e0 = floor(B.log_hi * 1.44269504088896338700);
+                const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
+                B.scale_e2 = e0;
+                B.scale_m = 1.0 + sg_expm1_d(rr);
+                A.bases[g] = B;
+                sh_b = B;
+            }
         }
-        if (lane == 0) A.bases[g] = B;
         if (!A.do_items) return;
-        __syncwarp();
-        for (int t = A.int_item_ptr[g] + lane; t < A.int_item_ptr[g + 1]; t += 32) {
+        __syncthreads();
+        const SgBaseDev B = sh_b;
+        for (int t = A.int_item_ptr[g] + threadIdx.x; t < A.int_item_ptr[g + 1]; t += blockDim.x) {
             const int it = A.int_items[t];
             A.vars[it] = item_values(A.roles[it], G, B, A.params);
             if (A.items[it].nchunk == 0)
@@ -701,7 +741,7 @@ __global__ void sg_grad_kernel(SgGradArgs A) {
 
 cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s) {
     const int threads = 256;
-    const int nbase = (a.nintegrals + 7) / 8;
+    const int nbase = a.nintegrals;  // one block per integral
     long long eblocks = (a.nentries + threads - 1) / threads;
     if (eblocks > 152 * 16) eblocks = 152 * 16;
     if (eblocks < 1) eblocks = 1;
@@ -711,7 +751,7 @@ cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s) {
 
 static size_t fold_smem(int prec, int warps) {
     const size_t psz = prec == 1 ? sizeof(float2) : (prec == 2 ? sizeof(float4) : sizeof(double2));
-    return (size_t)warps * (SG_APAD * psz + SG_MAX_R * sizeof(int));
+    return (size_t)warps * (SG_APAD * psz + SG_MAX_R * (sizeof(SgPrefixPos) + sizeof(int)));
 }
 
 int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
@@ -793,13 +833,9 @@ __global__ void __launch_bounds__(256) sg_ceiling_kernel(int sweeps, double *out
                 habs = fmaf(fabsf(w), fabsf(D), habs);
             }
         } else {
+            // as the FP64 fold: one sum, the weighted deviation, one FMA
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const double s = S + dl[k], w = W * wl[k];
-                const double D = gdev_d<GK>(s, sphi, cphi, ph);
-                acc = fma(w, D, acc);
-                aabs = fma(fabs(w), fabs(D), aabs);
-            }
+            for (int k = 0; k < 8; k++) acc = fma(W, gdevw_d<GK>(S + dl[k], wl[k], sphi, cphi, ph), acc);
         }
         S += (T)1e-7;
     }

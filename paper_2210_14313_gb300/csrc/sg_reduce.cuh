@@ -1,10 +1,12 @@
-// Deterministic reduction of the fold's chunk slots on the device: per-lane
-// compensated sums, the xor-butterfly lane combine, the two-level ticketing
-// of complete_chunk and the assembly of an item's output record.  Shared by
+// Deterministic reduction of the fold's chunk slots on the device: exact
+// sums in a 128-bit integer window (sg_xsum.h) across the lanes of a warp,
+// the two-level ticketing of complete_chunk and the assembly of an item's
+// output record.  Shared by
 // the built-in fold kernels and the fold kernel compiled at run time for a
 // user integrand (so it compiles under nvcc and NVRTC alike).
 #pragma once
 #include "sg_internal.h"
+#include "sg_xsum.h"
 
 #define SG_FULL_MASK 0xffffffffu
 
@@ -48,89 +50,78 @@ __device__ inline void assemble_item(const SgItemDev *items, const SgItemVar *va
     if (flags && guard_tol > 0.0) flags[item] = o.err_est > guard_tol ? 1 : 0;
 }
 
-// Combines the lanes' compensated pairs (s, c) and absolute sums with an
-// xor butterfly: at level o, lane l merges with lane l ^ o.  TwoSum returns
-// the exact rounding error of s_l + s_m, which does not depend on the order
-// of its operands, so both partners compute bitwise the same pair and every
-// lane ends with the same result; the tree is fixed, so the result does not
-// depend on which warp runs it.  Five levels of dependent FP64 work instead
-// of a 32-step lane-serial sum.
-// (s, c) += (s2, c2) for compensated pairs; symmetric in its two operands.
-__device__ __forceinline__ void pair_add(double &s, double &c, double s2, double c2) {
-    const double t = __dadd_rn(s, s2);
-    const double z = __dsub_rn(t, s);
-    const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(s2, z));
-    s = t;
-    c = __dadd_rn(__dadd_rn(c, c2), e);
-}
+// Warp-wide exact sums (sg_xsum.h): the largest exponent among the lanes'
+// terms fixes the unit; the lanes' 128-bit partial sums are added by an xor
+// butterfly of integer additions, which gives every lane the same total in
+// any order; the total is rounded once to a pair (s, c).
+__device__ __forceinline__ int warp_max_exp(int e) { return (int)__reduce_max_sync(SG_FULL_MASK, (unsigned)e); }
 
-__device__ __forceinline__ void lane_combine(double &s, double &c, double &ab) {
+__device__ __forceinline__ void warp_xsum(SgX a, int E, double &s, double &c) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double s2 = __shfl_xor_sync(SG_FULL_MASK, s, o);
-        const double c2 = __shfl_xor_sync(SG_FULL_MASK, c, o);
-        const double a2 = __shfl_xor_sync(SG_FULL_MASK, ab, o);
-        pair_add(s, c, s2, c2);
-        ab = __dadd_rn(ab, a2);
+    for (int o = 16; o > 0; o >>= 1) {
+        SgX b;
+        b.lo = __shfl_xor_sync(SG_FULL_MASK, a.lo, o);
+        b.hi = __shfl_xor_sync(SG_FULL_MASK, a.hi, o);
+        sg_x_plus(a, b);
     }
+    sg_x_pair(a, E, &s, &c);
 }
 
-// Lane l adds x[l], x[l+32], ... into four compensated accumulators (the
-// t-th load of a batch into accumulator t mod 4, four independent chains),
-// which are then merged and the lanes combined by lane_combine: a fixed
-// summation order whichever warp runs it.  Each lane issues its loads eight
-// at a time (missing ones read as zero, which leaves a compensated sum
-// unchanged), so that the L2 latency is paid once per batch.
+// The exact sum of one double per lane, rounded to the nearest double.
+__device__ __forceinline__ double warp_sum(double v) {
+    const int E = warp_max_exp(sg_x_exp(v));
+    SgX a = {0ull, 0ull};
+    sg_x_add(a, v, E);
+    double s, c;
+    warp_xsum(a, E, s, c);
+    return s;
+}
+
+// Sum of a group's chunk slots (sum, abs): lane l takes slots l, l + 32, ...;
+// a first pass finds the largest exponents, a second adds the terms.
 __device__ inline void reduce_slots(const double2 *slots, unsigned long long n, int lane, double &S,
                              double &C, double &AB) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0}, ab = 0.0;
-    for (unsigned long long q0 = lane; q0 < n; q0 += 8 * 32) {
-        double2 v[8];
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-            const unsigned long long q = q0 + t * 32;
-            v[t] = q < n ? __ldcg(slots + q) : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-            neu_add(s[t & 3], c[t & 3], v[t].x);
-            ab += v[t].y;
-        }
+    int Es = 1, Ea = 1;
+    for (unsigned long long q = lane; q < n; q += 32) {
+        const double2 v = __ldcg(slots + q);
+        Es = max(Es, sg_x_exp(v.x));
+        Ea = max(Ea, sg_x_exp(v.y));
     }
-    pair_add(s[0], c[0], s[1], c[1]);
-    pair_add(s[2], c[2], s[3], c[3]);
-    pair_add(s[0], c[0], s[2], c[2]);
-    lane_combine(s[0], c[0], ab);
-    S = s[0];
-    C = c[0];
-    AB = ab;
+    Es = warp_max_exp(Es);
+    Ea = warp_max_exp(Ea);
+    SgX as = {0ull, 0ull}, aa = {0ull, 0ull};
+    for (unsigned long long q = lane; q < n; q += 32) {
+        const double2 v = __ldcg(slots + q);
+        sg_x_add(as, v.x, Es);
+        sg_x_add(aa, v.y, Ea);
+    }
+    double ac;
+    warp_xsum(as, Es, S, C);
+    warp_xsum(aa, Ea, AB, ac);
 }
 
-// Same over group records (s, c, abs).
+// Same over group records: s and c of every group in one sum, abs in another.
 __device__ inline void reduce_groups(const SgGroupSlot *g, unsigned long long n, int lane, double &S,
                               double &C, double &AB) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0}, ab = 0.0;
-    for (unsigned long long q0 = lane; q0 < n; q0 += 8 * 32) {
-        double2 v[8], w[8];
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-            const unsigned long long q = q0 + t * 32;
-            v[t] = q < n ? __ldcg((const double2 *)(g + q)) : make_double2(0.0, 0.0);
-            w[t] = q < n ? __ldcg((const double2 *)(g + q) + 1) : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-            pair_add(s[t & 3], c[t & 3], v[t].x, v[t].y);
-            ab += w[t].x;
-        }
+    int Es = 1, Ea = 1;
+    for (unsigned long long q = lane; q < n; q += 32) {
+        const double2 v = __ldcg((const double2 *)(g + q));
+        const double a = __ldcg(&g[q].abs);
+        Es = max(Es, max(sg_x_exp(v.x), sg_x_exp(v.y)));
+        Ea = max(Ea, sg_x_exp(a));
     }
-    pair_add(s[0], c[0], s[1], c[1]);
-    pair_add(s[2], c[2], s[3], c[3]);
-    pair_add(s[0], c[0], s[2], c[2]);
-    lane_combine(s[0], c[0], ab);
-    S = s[0];
-    C = c[0];
-    AB = ab;
+    Es = warp_max_exp(Es);
+    Ea = warp_max_exp(Ea);
+    SgX as = {0ull, 0ull}, aa = {0ull, 0ull};
+    for (unsigned long long q = lane; q < n; q += 32) {
+        const double2 v = __ldcg((const double2 *)(g + q));
+        sg_x_add(as, v.x, Es);
+        sg_x_add(as, v.y, Es);
+        sg_x_add(aa, __ldcg(&g[q].abs), Ea);
+    }
+    double ac;
+    warp_xsum(as, Es, S, C);
+    warp_xsum(aa, Ea, AB, ac);
 }
 
 // Called by the warp that wrote chunk c's slot.  Two-level ticketing: the

@@ -80,10 +80,10 @@ extern "C" sg_status sg_integrand_create(const char *source, int state_size, sg_
     f->K = state_size;
     f->device = dev;
     std::string prog = std::string(source) + "\n#include \"sg_user_kernel.cuh\"\n";
-    const char *hdr_src[] = {sg_src_internal, sg_src_fold_logic, sg_src_reduce, sg_src_user_kernel};
-    const char *hdr_names[] = {"sg_internal.h", "sg_fold_logic.h", "sg_reduce.cuh", "sg_user_kernel.cuh"};
+    const char *hdr_src[] = {sg_src_internal, sg_src_fold_logic, sg_src_xsum, sg_src_reduce, sg_src_user_kernel};
+    const char *hdr_names[] = {"sg_internal.h", "sg_fold_logic.h", "sg_xsum.h", "sg_reduce.cuh", "sg_user_kernel.cuh"};
     nvrtcProgram P = nullptr;
-    if (N.create(&P, prog.c_str(), "sg_user.cu", 4, hdr_src, hdr_names) != NVRTC_SUCCESS) {
+    if (N.create(&P, prog.c_str(), "sg_user.cu", 5, hdr_src, hdr_names) != NVRTC_SUCCESS) {
         delete f;
         return SG_ENOMEM;
     }

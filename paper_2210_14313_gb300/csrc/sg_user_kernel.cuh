@@ -145,7 +145,7 @@ extern "C" __global__ void sg_user_fold(SgFoldArgs A, SgUserArgs U) {
                 __syncwarp();
             }
         }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(SG_FULL_MASK, acc, o);
+        acc = warp_sum(acc);
         if (lane == 0) {
             SgSlot sl;
             sl.sum = acc * P->coef;

@@ -78,13 +78,34 @@ def block(kind, bk, k):
     return x[:n].copy(), w[:n].copy()
 
 
-def fixed(kind, x, phi=0.0):
+def fixed(kind, x, phi=0.0, w=None):
     """The FP64 fold's fixed-point functions built for the host (sg_fixed.h):
-    kind 0 expm1, kind 1 (sin, cos) pairs, kind 2 sin(x) sin(phi + x)."""
+    kind 0 expm1, kind 1 (sin, cos) pairs, kind 2 sin(x) sin(phi + x),
+    kind 3 w sin(x) sin(phi + x), kind 4 w expm1(x)."""
     lib = _load()
     dp = ctypes.POINTER(ctypes.c_double)
-    lib.chk_fixed.argtypes = [ctypes.c_int, dp, dp, ctypes.c_longlong, ctypes.c_double]
+    lib.chk_fixed.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_longlong, ctypes.c_double]
     x = np.ascontiguousarray(x, dtype=np.float64)
+    wv = np.ascontiguousarray(np.ones_like(x) if w is None else w, dtype=np.float64)
     y = np.zeros(len(x) * (2 if kind == 1 else 1))
-    lib.chk_fixed(kind, x.ctypes.data_as(dp), y.ctypes.data_as(dp), len(x), phi)
+    lib.chk_fixed(kind, x.ctypes.data_as(dp), wv.ctypes.data_as(dp), y.ctypes.data_as(dp), len(x), phi)
     return y
+
+
+def xsum(v):
+    """(s, c) of the reduction's exact 128-bit window sum of v (sg_xsum.h)."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_xsum.argtypes = [dp, ctypes.c_longlong, dp]
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(2)
+    lib.chk_xsum(v.ctypes.data_as(dp), len(v), out.ctypes.data_as(dp))
+    return out[0], out[1]
+
+
+def divmagic_mismatches(mmax):
+    """Mismatches of the kernels' divide-free q / m for m <= mmax."""
+    lib = _load()
+    lib.chk_divmagic.restype = ctypes.c_longlong
+    lib.chk_divmagic.argtypes = [ctypes.c_int]
+    return lib.chk_divmagic(mmax)

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../paper_2210_14313_gb300/csrc/sg_fixed.h"
+#include "../../paper_2210_14313_gb300/csrc/sg_xsum.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_fold_logic.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_plan.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_rules.h"
@@ -213,7 +214,11 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
                 for (int tt = r - 2; tt >= 0; tt--) {
                     const int dir = sg_actual_dir(idx[tt], skip);
                     if (dir == skip || dir >= dd + (skip >= 0)) violations++;
+                    // the kernels' divide-free digit (magic multiplier) must agree
+                    const int q0 = q, mm = Pp->pm[tt];
+                    const int qm = sg_div_magic_q(q0, sg_div_magic(mm));
                     const long long rel = sg_prefix_entry(Pp, tt, dir, &q);
+                    if (qm != q || Pp->poff[tt] + (long long)dir * mm + (q0 - qm * mm) != rel) violations++;
                     if (check(rel, Pp->poff[tt], Pp->pm[tt])) {
                         s += tab[tbase + rel].x;
                         w *= tab[tbase + rel].y;
@@ -345,20 +350,52 @@ int chk_rule(int kind, int level, double *x, double *w) { return sg_rule_level(k
 int chk_block(int kind, int bk, int k, double *x, double *w) { return sg_block(kind, bk, k, x, w); }
 
 // The fixed-point elementary functions of the FP64 fold (sg_fixed.h), built
-// for the host: kind 0: expm1(x) for |x| <= ln2/2;
-// kind 1: sin and cos for |x| <= 0.7854 (y holds pairs); kind 2:
-// sin(x) sin(phi + x) with phi = params[0].
-void chk_fixed(int kind, const double *x, double *y, long long n, double phi) {
+// for the host: kind 0: expm1(x) for |x| <= ln2/2; kind 1: sin and cos for
+// |x| <= 0.7854 (y holds pairs); kind 2: sin(x) sin(phi + x); kind 3:
+// w sin(x) sin(phi + x); kind 4: w expm1(x) (w may be NULL for kinds 0-2).
+void chk_fixed(int kind, const double *x, const double *w, double *y, long long n, double phi) {
     const SgFxPhase ph = sg_fx_phase(sin(phi), cos(phi));
     for (long long i = 0; i < n; i++) {
         if (kind == 0) {
             y[i] = sg_fx_expm1(x[i]);
         } else if (kind == 1) {
             sg_fx_sincos(x[i], &y[2 * i], &y[2 * i + 1]);
-        } else {
+        } else if (kind == 2) {
             y[i] = sg_fx_osc_dev(x[i], ph);
+        } else if (kind == 3) {
+            y[i] = sg_fx_osc_dev_w(x[i], w[i], ph);
+        } else {
+            y[i] = sg_fx_expm1_w(x[i], w[i]);
         }
     }
+}
+
+// Mismatches of the divide-free q / m (sg_div_magic) for m in [1, mmax] and
+// q in a sample of [0, 2^31): every q < 4096, the ends, and a multiplicative
+// sequence.
+long long chk_divmagic(int mmax) {
+    long long bad = 0;
+    for (int m = 1; m <= mmax; m++) {
+        const SgDivMagic g = sg_div_magic(m);
+        for (long long q = 0; q < 4096; q++)
+            if (sg_div_magic_q((int)q, g) != (int)(q / m)) bad++;
+        for (long long q = 4096; q < 0x7fffffffll; q = q * 9 / 7 + 13)
+            if (sg_div_magic_q((int)q, g) != (int)(q / m)) bad++;
+        const long long ends[] = {0x7fffffffll, 0x7ffffffell, (0x7fffffffll / m) * m, (0x7fffffffll / m) * m - 1};
+        for (long long q : ends)
+            if (q >= 0 && sg_div_magic_q((int)q, g) != (int)(q / m)) bad++;
+    }
+    return bad;
+}
+
+// The reduction's exact 128-bit window sum (sg_xsum.h) of v[0..n), in the
+// order given: out = (s, c).
+void chk_xsum(const double *v, long long n, double *out) {
+    int E = 1;
+    for (long long i = 0; i < n; i++) E = sg_x_exp(v[i]) > E ? sg_x_exp(v[i]) : E;
+    SgX a = {0ull, 0ull};
+    for (long long i = 0; i < n; i++) sg_x_add(a, v[i], E);
+    sg_x_pair(a, E, &out[0], &out[1]);
 }
 
 }  // extern "C"

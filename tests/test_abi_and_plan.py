@@ -161,12 +161,14 @@ def _nvrtc_compile(lib, source, k):
     import ctypes
     csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "paper_2210_14313_gb300", "csrc")
-    names = ["sg_internal.h", "sg_fold_logic.h", "sg_reduce.cuh", "sg_user_kernel.cuh"]
+    from paper_2210_14313_gb300 import _build
+    names = [n for _, n in _build.EMBEDDED]
     hdrs = [open(os.path.join(csrc, n)).read().encode() for n in names]
     prog = ctypes.c_void_p()
     src = (source + '\n#include "sg_user_kernel.cuh"\n').encode()
-    assert lib.nvrtcCreateProgram(ctypes.byref(prog), src, b"sg_user.cu", 4, (ctypes.c_char_p * 4)(*hdrs),
-                                  (ctypes.c_char_p * 4)(*[n.encode() for n in names])) == 0
+    nh = len(names)
+    assert lib.nvrtcCreateProgram(ctypes.byref(prog), src, b"sg_user.cu", nh, (ctypes.c_char_p * nh)(*hdrs),
+                                  (ctypes.c_char_p * nh)(*[n.encode() for n in names])) == 0
     opts = [b"--gpu-architecture=sm_103", ("-DSG_USER_K=%d" % k).encode(), b"-std=c++17", b"-default-device"]
     rc = lib.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
     n = ctypes.c_size_t()
@@ -187,3 +189,9 @@ def test_user_integrand_programs_compile():
     assert rc == 0, log
     rc, log = _nvrtc_compile(lib, ui.BROKEN, 1)
     assert rc != 0 and "undefined_name" in log
+
+
+def test_divide_free_block_digits():
+    # the prefix digits' q / m by a multiplier (Granlund-Montgomery) for every
+    # block size up to 5000 nodes
+    assert index_check.divmagic_mismatches(5000) == 0

@@ -59,3 +59,48 @@ def test_oscillatory_deviation(phi):
     if abs(np.sin(phi)) > 0.1:
         assert rel <= 2.5 * U, float(rel / U)
     assert absw <= 2.0 ** -52, float(absw)
+
+
+def _weights(n, seed):
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(-1.0, 1.0, n) * 10.0 ** rng.uniform(-6, 0, n)
+    w[:4] = [0.0, 1.0, -1.0, 2.0 ** -1000]
+    return w
+
+
+def test_weighted_expm1():
+    # w expm1(x), rounded once from fixed point
+    mp.mp.dps = 40
+    x = _args(-0.3465, 0.3465, 3000, 4)
+    w = _weights(len(x), 5)
+    y = index_check.fixed(4, x, w=w)
+    worst = 0
+    for a, b, c in zip(x, w, y):
+        ref = mp.expm1(mp.mpf(a)) * mp.mpf(b)
+        if abs(ref) < 1e-290:
+            assert abs(c) < 1e-290
+            continue
+        worst = max(worst, abs((mp.mpf(c) - ref) / ref))
+    assert worst <= 1.0 * U, float(worst / U)
+
+
+@pytest.mark.parametrize("phi", [0.3, 2.0, -1.2, 4.0, 3.0, 1e-3])
+def test_weighted_oscillatory_deviation(phi):
+    mp.mp.dps = 40
+    x = _args(-0.7854, 0.7854, 1500, 6)
+    w = _weights(len(x), 7)
+    y = index_check.fixed(3, x, phi, w=w)
+    sp, cp = mp.mpf(float(np.sin(phi))), mp.mpf(float(np.cos(phi)))
+    rel = absw = 0
+    for a, b, c in zip(x, w, y):
+        X, Wt = mp.mpf(a), mp.mpf(b)
+        ref = Wt * mp.sin(X) * (sp * mp.cos(X) + cp * mp.sin(X))
+        scale = abs(Wt * mp.sin(X)) * (abs(sp * mp.cos(X)) + abs(cp * mp.sin(X)))
+        if scale < 1e-290:
+            assert abs(c) < 1e-290
+            continue
+        rel = max(rel, abs(mp.mpf(c) - ref) / scale)
+        absw = max(absw, abs(mp.mpf(c) - ref) / abs(X * Wt))
+    if abs(np.sin(phi)) > 0.1:
+        assert rel <= 2.0 * U, float(rel / U)
+    assert absw <= 2.0 ** -52, float(absw)

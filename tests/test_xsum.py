@@ -1,0 +1,50 @@
+"""The reduction's exact summation in a 128-bit integer window (sg_xsum.h),
+built for the host: against exact rational sums, independent of the order of
+the terms."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import index_check
+
+
+def _exact(v):
+    return sum((Fraction(float(x)) for x in v), Fraction(0))
+
+
+def _cases():
+    rng = np.random.default_rng(11)
+    yield rng.standard_normal(64)
+    yield rng.standard_normal(2048) * 10.0 ** rng.uniform(-12, 0, 2048)   # 40 binades
+    v = rng.standard_normal(1000)
+    yield np.concatenate([v, -v[::-1]])                                   # exact cancellation
+    yield np.array([1.0, 2.0 ** -53, 2.0 ** -53, -1.0])                    # rounding-tie residue
+    yield np.array([1e10, -1e10, 3.0, 1e-3])                               # cancellation, in the window
+    yield np.array([0.0, -0.0, 0.0])
+    yield rng.uniform(0, 1, 5000) * 1e-200
+
+
+@pytest.mark.parametrize("k", range(7))
+def test_window_sum_is_exact(k):
+    v = list(_cases())[k]
+    s, c = index_check.xsum(v)
+    ex = _exact(v)
+    # s is the double nearest the exact sum, s + c carries the rest
+    assert s == float(ex)
+    rest = ex - Fraction(s)
+    assert c == float(rest)
+    # any order gives the same pair
+    rng = np.random.default_rng(k)
+    assert index_check.xsum(rng.permutation(v)) == (s, c)
+
+
+def test_terms_below_the_window_truncate_symmetrically():
+    # the window ends 2^-108 below the largest term: what cancels above it
+    # leaves only what lies inside it
+    assert index_check.xsum(np.array([1e300, -1e300, 3.0, 1e-3])) == (0.0, 0.0)
+    # a term 2^-120 below the largest falls under the unit 2^-(56 + 52) of it
+    v = np.array([1.0, 2.0 ** -120, -(2.0 ** -120)])
+    assert index_check.xsum(v) == (1.0, 0.0)
+    v = np.array([1.0, 2.0 ** -120])
+    assert index_check.xsum(v) == (1.0, 0.0)
