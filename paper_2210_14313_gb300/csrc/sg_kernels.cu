@@ -548,41 +548,44 @@ __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase)
     cudaTriggerProgrammaticLaunchCompletion();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((int)blockIdx.x < nbase) {
-        __shared__ double sh_s[8], sh_c[8];
+        __shared__ SgX sh_x[8];
+        __shared__ int sh_e[8];
         __shared__ SgBaseDev sh_b;
         const int g = blockIdx.x;
         const SgIntegralDev G = A.integrals[g];
         const double *a = A.params + G.param_off, *u = a + G.d;
-        double s = 0.0, c = 0.0;
+        // log f(c) (or the centre phase) as an exact sum in a 128-bit window
+        // (sg_xsum.h): each thread keeps a running sum of its terms, whose
+        // unit follows the largest term so far; the block then aligns the
+        // threads' sums to the largest unit and adds them as integers.  The
+        // result is the same on every call, and no FP64 operation sits in a
+        // dependency chain (on GB300 each would cost ~10^2 cycles).
+        SgX acc = {0ull, 0ull};
+        int E = 1;
         if (G.fam != SG_FAM_USER)  // a user integrand's parameters have no fixed layout
-            for (int i = threadIdx.x; i < G.d; i += blockDim.x) neu_add(s, c, phi_centre(G.fam, a[i], u[i]));
-        // combine compensated pairs by a fixed tree: at level o the lower lane
-        // of each pair adds the upper one's pair.  GB300 runs FP64 at a rate
-        // per active lane, so the steps, and the scalar work below, run on
-        // the lanes that need them only.
-        for (int o = 1; o < 32; o <<= 1) {
-            const double so = __shfl_down_sync(FULL_MASK, s, o), co = __shfl_down_sync(FULL_MASK, c, o);
-            if ((lane & (2 * o - 1)) == 0) {
-                neu_add(s, c, so);
-                c += co;
-            }
+            for (int i = threadIdx.x; i < G.d; i += blockDim.x)
+                sg_x_add_adaptive(acc, E, phi_centre(G.fam, a[i], u[i]));
+        const int Ew = warp_max_exp(E);
+        if (lane == 0) sh_e[warp] = Ew;
+        __syncthreads();
+        int Eb = sh_e[0];
+        for (int w = 1; w < nw; w++) Eb = max(Eb, sh_e[w]);
+        sg_x_shr(acc, Eb - E);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            SgX b;
+            b.lo = __shfl_xor_sync(FULL_MASK, acc.lo, o);
+            b.hi = __shfl_xor_sync(FULL_MASK, acc.hi, o);
+            sg_x_plus(acc, b);
         }
-        if (lane == 0) {
-            sh_s[warp] = s;
-            sh_c[warp] = c;
-        }
+        if (lane == 0) sh_x[warp] = acc;
         __syncthreads();
         if (warp == 0) {
-            s = lane < nw ? sh_s[lane] : 0.0;
-            c = lane < nw ? sh_c[lane] : 0.0;
-            for (int o = 1; o < nw; o <<= 1) {
-                const double so = __shfl_down_sync(FULL_MASK, s, o), co = __shfl_down_sync(FULL_MASK, c, o);
-                if ((lane & (2 * o - 1)) == 0) {
-                    neu_add(s, c, so);
-                    c += co;
-                }
-            }
             if (lane == 0) {
+                SgX t = sh_x[0];
+                for (int w = 1; w < nw; w++) sg_x_plus(t, sh_x[w]);
+                double s, c;
+                sg_x_pair(t, Eb, &s, &c);
                 SgBaseDev B;
                 if (G.fam == 1) {
                     B.log_hi = 0.0;

@@ -88,6 +88,35 @@ SG_XS void sg_x_add(SgX &a, double v, int E) {
     a.hi += hi + (a.lo < lo);
 }
 
+// a >>= k, arithmetic (towards minus infinity), k >= 0: moves a sum to a
+// coarser unit
+SG_XS void sg_x_shr(SgX &a, int k) {
+    if (k <= 0) return;
+    const unsigned long long sgn = (unsigned long long)((long long)a.hi >> 63);
+    if (k >= 128) {
+        a.lo = sgn;
+        a.hi = sgn;
+    } else if (k >= 64) {
+        a.lo = (unsigned long long)((long long)a.hi >> (k - 64));
+        a.hi = sgn;
+    } else {
+        a.lo = (a.lo >> k) | (a.hi << (64 - k));
+        a.hi = (unsigned long long)((long long)a.hi >> k);
+    }
+}
+
+// A running sum whose unit follows the largest exponent seen so far: a new
+// larger term first moves the sum to the coarser unit.  The result depends
+// only on the order of the terms (fixed by the caller), not on timing.
+SG_XS void sg_x_add_adaptive(SgX &a, int &E, double v) {
+    const int e = sg_x_exp(v);
+    if (e > E) {
+        sg_x_shr(a, e - E);
+        E = e;
+    }
+    sg_x_add(a, v, E);
+}
+
 SG_XS void sg_x_plus(SgX &a, const SgX &b) {
     a.lo += b.lo;
     a.hi += b.hi + (a.lo < b.lo);

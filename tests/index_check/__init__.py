@@ -109,3 +109,14 @@ def divmagic_mismatches(mmax):
     lib.chk_divmagic.restype = ctypes.c_longlong
     lib.chk_divmagic.argtypes = [ctypes.c_int]
     return lib.chk_divmagic(mmax)
+
+
+def xsum_adaptive(v, nthreads):
+    """(s, c) of the setup kernel's adaptive-unit window sums over nthreads."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_xsum_adaptive.argtypes = [dp, ctypes.c_longlong, ctypes.c_int, dp]
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(2)
+    lib.chk_xsum_adaptive(v.ctypes.data_as(dp), len(v), nthreads, out.ctypes.data_as(dp))
+    return out[0], out[1]

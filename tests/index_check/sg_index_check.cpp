@@ -398,4 +398,21 @@ void chk_xsum(const double *v, long long n, double *out) {
     sg_x_pair(a, E, &out[0], &out[1]);
 }
 
+// The setup kernel's scheme: nthreads running sums with adaptive units over
+// the terms i = t, t + nthreads, ..., aligned to the largest unit and added.
+void chk_xsum_adaptive(const double *v, long long n, int nthreads, double *out) {
+    std::vector<SgX> acc(nthreads, SgX{0ull, 0ull});
+    std::vector<int> E(nthreads, 1);
+    for (int t = 0; t < nthreads; t++)
+        for (long long i = t; i < n; i += nthreads) sg_x_add_adaptive(acc[t], E[t], v[i]);
+    int Eb = 1;
+    for (int t = 0; t < nthreads; t++) Eb = E[t] > Eb ? E[t] : Eb;
+    SgX tot = {0ull, 0ull};
+    for (int t = 0; t < nthreads; t++) {
+        sg_x_shr(acc[t], Eb - E[t]);
+        sg_x_plus(tot, acc[t]);
+    }
+    sg_x_pair(tot, Eb, &out[0], &out[1]);
+}
+
 }  // extern "C"

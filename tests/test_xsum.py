@@ -48,3 +48,17 @@ def test_terms_below_the_window_truncate_symmetrically():
     assert index_check.xsum(v) == (1.0, 0.0)
     v = np.array([1.0, 2.0 ** -120])
     assert index_check.xsum(v) == (1.0, 0.0)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 6])
+@pytest.mark.parametrize("nthreads", [1, 7, 256])
+def test_adaptive_units_match_the_exact_sum(k, nthreads):
+    # the setup kernel's running sums: units follow each thread's largest term;
+    # growing units truncate at most 2^-108 of the largest term per step
+    v = list(_cases())[k]
+    s, c = index_check.xsum_adaptive(v, nthreads)
+    ex = _exact(v)
+    big = max(abs(float(x)) for x in v) if len(v) else 0.0
+    err = abs(Fraction(s) + Fraction(c) - ex)
+    assert err <= Fraction(len(v)) * Fraction(big) * Fraction(2) ** -107
+    assert index_check.xsum_adaptive(v, nthreads) == (s, c)
