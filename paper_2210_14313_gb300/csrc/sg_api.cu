@@ -210,7 +210,7 @@ static void plan_free(Plan *P) {
 }
 
 // Resolves the rule-block pointers and copies a host plan to the device.
-static sg_status plan_upload(Plan *P) {
+static sg_status plan_upload(Plan *P, const u64 *d_binom) {
     cudaGetDevice(&P->device);
     // device copy, one allocation
     size_t sz = 0;
@@ -226,6 +226,7 @@ static sg_status plan_upload(Plan *P) {
     const size_t o_iv = carve<int>(sz, P->int_items.size() + 1);
     const size_t o_do = carve<int>(sz, P->delta_off.size() + 1);
     const size_t o_dm = carve<int>(sz, P->delta_m.size() + 1);
+    const size_t o_cs = carve<SgChunkStart>(sz, (size_t)P->nchunks);
     std::vector<unsigned char> host(sz, 0);
     memcpy(&host[o_int], P->integrals.data(), P->integrals.size() * sizeof(SgIntegralDev));
     memcpy(&host[o_blk], P->blocks.data(), P->blocks.size() * sizeof(SgBlockDev));
@@ -260,15 +261,25 @@ static sg_status plan_upload(Plan *P) {
     P->d_delta_off = (int *)(b + o_do);
     P->d_delta_m = (int *)(b + o_dm);
     P->d_delta_xw = P->reqs[0].rule->d_xw;
+    // chunk starts: unranked once per plan on the device (the legacy stream,
+    // like the copy above, and waited for, since callers' streams may not
+    // synchronise with it)
+    P->d_chunk_start = (SgChunkStart *)(b + o_cs);
+    if (P->nchunks > 0) {
+        if (sg_launch_chunk_starts(P->d_items, P->d_pats, P->d_pat_chunk0, (long long)P->pats.size(), P->nchunks,
+                                   d_binom, P->d_chunk_start, 0) != cudaSuccess ||
+            cudaStreamSynchronize(0) != cudaSuccess)
+            return SG_ECUDA;
+    }
     return SG_OK;
 }
 
 static sg_status build_plan(const std::vector<Req> &reqs, int prec, const sg_tuning &tune,
-                            long long warps, Plan **out) {
+                            long long warps, const u64 *d_binom, Plan **out) {
     Plan *P = nullptr;
     sg_status st = build_plan_host(reqs, prec, tune, warps, &P);
     if (st != SG_OK) return st;
-    st = plan_upload(P);
+    st = plan_upload(P, d_binom);
     if (st != SG_OK) {
         plan_free(P);
         return st;
@@ -334,7 +345,7 @@ static sg_status get_plan(const std::vector<Req> &reqs, int prec, Plan **out) {
         return SG_OK;
     }
     Plan *P = nullptr;
-    st = build_plan(reqs, prec, k.t, resident_warps(C, prec, k.t), &P);
+    st = build_plan(reqs, prec, k.t, resident_warps(C, prec, k.t), C->binom, &P);
     if (st != SG_OK) return st;
     if (g_plans.size() > 256) {  // bound the cache
         cudaDeviceSynchronize();
@@ -598,6 +609,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     fa.nitems = nitems;
     fa.pats = P->d_pats;
     fa.pat_chunk0 = P->d_pat_chunk0;
+    fa.chunk_start = P->d_chunk_start;
     fa.npat = (long long)P->pats.size();
     fa.nchunks = P->nchunks;
     fa.tab = prec == 1 ? W->tab32.p : (prec == 2 ? W->tabff.p : W->tab64.p);

@@ -126,6 +126,14 @@ struct SgBaseDev {
 };
 
 // Arguments of a fold kernel (the built-in ones and a compiled user integrand's).
+// Where chunk c starts: its pattern and the first r-subset of its span
+// (enumerated directions), unranked once per plan on the device.
+struct alignas(32) SgChunkStart {
+    int pat;
+    unsigned short idx[SG_MAX_R];
+    int pad;
+};
+
 struct SgFoldArgs {
     const SgItemDev *items;
     const SgItemVar *vars;           // per item, filled by the setup kernel
@@ -133,6 +141,7 @@ struct SgFoldArgs {
     const SgPatDev *pats;
     const unsigned long long *pat_chunk0;  // per pattern, ascending
     long long npat;
+    const SgChunkStart *chunk_start; // per chunk (NULL: found by search and unranking)
     unsigned long long nchunks;
     const void *tab;                 // float2* or double2*
     const unsigned long long *binom; // [k][n] table

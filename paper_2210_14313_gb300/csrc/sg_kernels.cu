@@ -374,7 +374,11 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     unsigned long long rank, cnt;
     int a_lo, a_hi;
     sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
-    unrank_warp(rank, d, r, A.binom, sIdx, lane);
+    if (A.chunk_start) {
+        if (lane < r) sIdx[lane] = __ldg(&A.chunk_start[c].idx[lane]);
+    } else {
+        unrank_warp(rank, d, r, A.binom, sIdx, lane);
+    }
     // everything above reads only the plan; the tables and item values come
     // from the setup kernel, which may still be finishing (programmatic
     // dependent launch).  One wait per warp suffices: once it returns the
@@ -463,10 +467,14 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         if (c >= A.nchunks) break;
         // pattern of chunk c: last pattern with chunk0 <= c
         long long lo = 0, hi = A.npat - 1;
-        while (lo < hi) {
-            long long mid = (lo + hi + 1) >> 1;
-            if (__ldg(A.pat_chunk0 + mid) <= c) lo = mid;
-            else hi = mid - 1;
+        if (A.chunk_start) {
+            lo = __ldg(&A.chunk_start[c].pat);
+        } else {
+            while (lo < hi) {
+                long long mid = (lo + hi + 1) >> 1;
+                if (__ldg(A.pat_chunk0 + mid) <= c) lo = mid;
+                else hi = mid - 1;
+            }
         }
         const SgPatDev *P = A.pats + lo;
         const int item = P->item;
@@ -658,6 +666,42 @@ __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase)
             A.tabff[B.off + local] = make_float4(fp.hi, fp.lo, fw.hi, fw.lo);
         }
     }
+}
+
+// One thread per chunk: its pattern (last pattern whose first chunk is <= c)
+// and the first subset of its span, unranked (lexicographic order).
+__global__ void sg_chunk_start_kernel(const SgItemDev *items, const SgPatDev *pats,
+                                      const unsigned long long *pat_chunk0, long long npat,
+                                      unsigned long long nchunks, const unsigned long long *binom,
+                                      SgChunkStart *out) {
+    for (unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = npat - 1;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if (pat_chunk0[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const SgPatDev *P = pats + lo;
+        unsigned long long rank, cnt;
+        int a_lo, a_hi, idx[SG_MAX_R];
+        sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
+        sg_unrank_lex(rank, items[P->item].d, P->r, binom, idx);
+        SgChunkStart cs;
+        cs.pat = (int)lo;
+        for (int t = 0; t < SG_MAX_R; t++) cs.idx[t] = (unsigned short)(t < P->r ? idx[t] : 0);
+        cs.pad = 0;
+        out[c] = cs;
+    }
+}
+
+cudaError_t sg_launch_chunk_starts(const SgItemDev *items, const SgPatDev *pats, const unsigned long long *pat_chunk0,
+                                   long long npat, unsigned long long nchunks, const unsigned long long *binom,
+                                   SgChunkStart *out, cudaStream_t s) {
+    if (nchunks == 0) return cudaSuccess;
+    const unsigned long long blocks = (nchunks + 255) / 256 < 4096 ? (nchunks + 255) / 256 : 4096;
+    sg_chunk_start_kernel<<<(unsigned)blocks, 256, 0, s>>>(items, pats, pat_chunk0, npat, nchunks, binom, out);
+    return cudaGetLastError();
 }
 
 __global__ void sg_prep_kernel(SgPrepArgs A) {

@@ -56,6 +56,11 @@ struct SgSetupArgs {
 
 
 
+// Fills the per-chunk start records of a plan (pattern and first subset).
+cudaError_t sg_launch_chunk_starts(const SgItemDev *items, const SgPatDev *pats, const unsigned long long *pat_chunk0,
+                                   long long npat, unsigned long long nchunks, const unsigned long long *binom,
+                                   SgChunkStart *out, cudaStream_t s);
+
 #define SG_APAD 128  // prefix states per warp held in shared memory
 
 // Grid sizing of the persistent fold kernel.

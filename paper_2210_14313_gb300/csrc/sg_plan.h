@@ -81,6 +81,7 @@ struct Plan {
     int *d_int_item_ptr = nullptr, *d_int_items = nullptr;
     SgPatDev *d_pats = nullptr;
     u64 *d_pat_chunk0 = nullptr;
+    SgChunkStart *d_chunk_start = nullptr;  // per chunk, filled on the device at upload
     int *d_delta_off = nullptr, *d_delta_m = nullptr;
     double2 *d_delta_xw = nullptr;  // the rule's block array (borrowed)
     int launch_ctas = 0;

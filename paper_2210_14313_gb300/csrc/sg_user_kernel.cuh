@@ -79,10 +79,14 @@ extern "C" __global__ void sg_user_fold(SgFoldArgs A, SgUserArgs U) {
         c = __shfl_sync(SG_FULL_MASK, c, 0);
         if (c >= A.nchunks) break;
         long long lo = 0, hi = A.npat - 1;
-        while (lo < hi) {
-            const long long mid = (lo + hi + 1) >> 1;
-            if (__ldg(A.pat_chunk0 + mid) <= c) lo = mid;
-            else hi = mid - 1;
+        if (A.chunk_start) {
+            lo = __ldg(&A.chunk_start[c].pat);
+        } else {
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if (__ldg(A.pat_chunk0 + mid) <= c) lo = mid;
+                else hi = mid - 1;
+            }
         }
         const SgPatDev *P = A.pats + lo;
         const int item = P->item;
@@ -91,7 +95,11 @@ extern "C" __global__ void sg_user_fold(SgFoldArgs A, SgUserArgs U) {
         unsigned long long rank, cnt;
         int a_lo, a_hi;
         sg_chunk_span(P, c, &rank, &cnt, &a_lo, &a_hi);
-        unrank_warp(rank, d, r, A.binom, sIdx, lane);
+        if (A.chunk_start) {
+            if (lane < r) sIdx[lane] = __ldg(&A.chunk_start[c].idx[lane]);
+        } else {
+            unrank_warp(rank, d, r, A.binom, sIdx, lane);
+        }
         if (!waited) {  // the tables come from the setup kernel (dependent launch)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             waited = true;
