@@ -168,7 +168,7 @@ extern "C" sg_status sg_rule_nodes(sg_rule r, int level, double *x, double *w, i
 // ---------------------------------------------------------------------------
 
 // index 0: FP64, 1: mixed, 2: float-float
-static sg_tuning g_tune[3] = {{2048, 4, 4}, {32768, 8, 4}, {32768, 8, 4}};
+static sg_tuning g_tune[3] = {{2048, 4, 8}, {32768, 8, 4}, {32768, 8, 4}};
 
 static bool prec_ok(int p) { return p == SG_PREC_FP64 || p == SG_PREC_MIXED || p == SG_PREC_FF; }
 

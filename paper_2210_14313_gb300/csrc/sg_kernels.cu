@@ -495,8 +495,9 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         }
         if (lane == 0) {
             SgSlot sl;
-            sl.sum = acc * P->coef;
-            sl.abs = aabs * fabs(P->coef);
+            const double cf = P->coef;  // 1 for most patterns: skip two dependent FP64 steps
+            sl.sum = cf == 1.0 ? acc : acc * cf;
+            sl.abs = cf == 1.0 ? aabs : aabs * fabs(cf);
             A.slots[c] = sl;
         }
         complete_chunk(A, item, c, lane);

@@ -271,12 +271,13 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     // above the tuned maximum, and at most 2^24 chunk slots
     const u64 warps = (u64)std::max<long long>(resident_warps, 1);
     // chunks per resident warp and the smallest chunk: a chunk's fixed work
-    // (grab, unranking, prefix folds, reduction) costs about 15k warp
-    // cycles, so chunks are a few per warp; the guided tail below evens out
-    // the end of the queue.  Values from sweeps on GB300 (cfg2/cfg3 FP64,
-    // cfg3 float, cfg2/cfg5 float-float).
+    // (grab, prefix folds, reduction and ticket) is thousands of warp
+    // cycles, so chunks are one (FP64, with 32 resident warps per SM) to
+    // four (float) per warp; the guided tail below evens out the end of the
+    // queue.  Values from sweeps on GB300 (cfg2/cfg3/cfg5 FP64, cfg3 float,
+    // cfg2/cfg5 float-float).
     const u64 floor_evals = prec == 0 ? 32 : 1024;
-    const u64 per_warp = prec == 1 ? 4 : 2;
+    const u64 per_warp = prec == 1 ? 4 : (prec == 2 ? 2 : 1);
     u64 target = total / (per_warp * warps) + 1;
     if (target < floor_evals) target = floor_evals;
     if (target > (u64)tune.points_per_chunk) target = (u64)tune.points_per_chunk;

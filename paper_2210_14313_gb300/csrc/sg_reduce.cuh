@@ -77,27 +77,34 @@ __device__ __forceinline__ double warp_sum(double v) {
     return s;
 }
 
-// Sum of a group's chunk slots (sum, abs): lane l takes slots l, l + 32, ...;
-// a first pass finds the largest exponents, a second adds the terms.
+// Sum of a group's chunk slots (sum, abs): at most SG_GROUP = 64 slots, two
+// per lane, held in registers while the largest exponents are found.
 __device__ inline void reduce_slots(const double2 *slots, unsigned long long n, int lane, double &S,
                              double &C, double &AB) {
-    int Es = 1, Ea = 1;
-    for (unsigned long long q = lane; q < n; q += 32) {
-        const double2 v = __ldcg(slots + q);
-        Es = max(Es, sg_x_exp(v.x));
-        Ea = max(Ea, sg_x_exp(v.y));
-    }
-    Es = warp_max_exp(Es);
-    Ea = warp_max_exp(Ea);
+    static_assert(SG_GROUP <= 64, "two slots per lane");
+    const double2 z = make_double2(0.0, 0.0);
+    const double2 v0 = (unsigned long long)lane < n ? __ldcg(slots + lane) : z;
+    const double2 v1 = (unsigned long long)lane + 32 < n ? __ldcg(slots + lane + 32) : z;
+    const int Es = warp_max_exp(max(sg_x_exp(v0.x), sg_x_exp(v1.x)));
+    const int Ea = warp_max_exp(max(sg_x_exp(v0.y), sg_x_exp(v1.y)));
     SgX as = {0ull, 0ull}, aa = {0ull, 0ull};
-    for (unsigned long long q = lane; q < n; q += 32) {
-        const double2 v = __ldcg(slots + q);
-        sg_x_add(as, v.x, Es);
-        sg_x_add(aa, v.y, Ea);
-    }
+    sg_x_add(as, v0.x, Es);
+    sg_x_add(as, v1.x, Es);
+    sg_x_add(aa, v0.y, Ea);
+    sg_x_add(aa, v1.y, Ea);
     double ac;
     warp_xsum(as, Es, S, C);
     warp_xsum(aa, Ea, AB, ac);
+}
+
+// Ticket increment with acquire-release semantics at GPU scope: the calling
+// thread's earlier writes become visible to whichever thread later reads the
+// incremented count, and the caller sees the writes released by the earlier
+// increments.
+__device__ __forceinline__ unsigned ticket_add(unsigned *p) {
+    unsigned v;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // Same over group records: s and c of every group in one sum, abs in another.
@@ -137,14 +144,14 @@ __device__ inline void complete_chunk(const SgFoldArgs &A, int item, unsigned lo
     const unsigned long long gfirst = g * SG_GROUP;
     const unsigned long long gsize =
         I->nchunk - gfirst < (unsigned long long)SG_GROUP ? I->nchunk - gfirst : SG_GROUP;
+    // lane 0 wrote the chunk's slot; its ticket releases it, and the last
+    // ticket of the group acquires all of the group's slots (the warp barrier
+    // passes the ordering on to the other lanes)
     unsigned int ticket = 0;
-    if (lane == 0) {
-        __threadfence();
-        ticket = atomicAdd(A.group_done + I->group0 + g, 1u);
-    }
+    if (lane == 0) ticket = ticket_add(A.group_done + I->group0 + g);
     ticket = __shfl_sync(SG_FULL_MASK, ticket, 0);
     if (ticket + 1ull != gsize) return;
-    __threadfence();
+    __syncwarp();
     double S, C, AB;
     reduce_slots((const double2 *)(A.slots + I->chunk0 + gfirst), gsize, lane, S, C, AB);
     if (lane == 0) {
@@ -154,12 +161,11 @@ __device__ inline void complete_chunk(const SgFoldArgs &A, int item, unsigned lo
         gs.abs = AB;
         gs.pad = 0.0;
         A.gslots[I->group0 + g] = gs;
-        __threadfence();
-        ticket = atomicAdd(A.item_done + item, 1u);
+        ticket = ticket_add(A.item_done + item);
     }
     ticket = __shfl_sync(SG_FULL_MASK, ticket, 0);
     if (ticket + 1ull != I->ngroups) return;
-    __threadfence();
+    __syncwarp();
     reduce_groups(A.gslots + I->group0, I->ngroups, lane, S, C, AB);
     if (lane == 0) finish(S + C, AB);
 }
