@@ -756,14 +756,23 @@ extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *par
         CK(cudaMemcpyAsync(W->params.p, params, 2 * (size_t)d * sizeof(double), cudaMemcpyHostToDevice, s));
         dp = (const double *)W->params.p;
     }
+    // the result record goes straight to the pinned host buffer, mapped into
+    // the device's address space: no separate copy back
+    void *mapped = nullptr;
+    if (cudaHostGetDevicePointer(&mapped, W->h_pinned, 0) != cudaSuccess) {
+        cudaGetLastError();
+        mapped = nullptr;
+    }
     CK(cudaEventRecord(W->ev0, s));
-    ST(run_plan(P, W, C, dp, 0.0, nullptr, s));
+    ST(run_plan(P, W, C, dp, 0.0, (SgOutDev *)mapped, s));
     CK(cudaEventRecord(W->ev1, s));
-    CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
+    if (!mapped) CK(cudaMemcpyAsync(W->h_pinned, W->out.p, sizeof(SgOutDev), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, W->ev0, W->ev1);
-    fill_result(*(SgOutDev *)W->h_pinned, P, 0, ms, out);
+    SgOutDev o;
+    memcpy(&o, W->h_pinned, sizeof(o));
+    fill_result(o, P, 0, ms, out);
     return SG_OK;
 }
 
