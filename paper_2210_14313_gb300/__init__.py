@@ -126,8 +126,12 @@ def _check(status: int, where: str):
 
 def _stream_handle(stream=None):
     import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+    if raw is not None:  # the current stream's handle without building a Stream object
+        return ctypes.c_void_p(raw(torch.cuda.current_device()))
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
 def _require_cuda():
@@ -195,6 +199,9 @@ class Result:
 
 def _params_arg(params, d):
     """(pointer, on_device, keepalive) for a params array of 2d doubles."""
+    if (type(params) is np.ndarray and params.dtype == np.float64 and params.flags.c_contiguous
+            and params.size == 2 * d):
+        return ctypes.c_void_p(params.ctypes.data), 0, params
     try:
         import torch
         if isinstance(params, torch.Tensor):

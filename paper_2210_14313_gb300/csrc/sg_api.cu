@@ -753,8 +753,19 @@ extern "C" sg_status sg_integrate(sg_rule rule, sg_family fam, const double *par
     ST(ensure_host(W, sizeof(SgOutDev)));
     const double *dp = params;
     if (!params_on_device) {
-        CK(cudaMemcpyAsync(W->params.p, params, 2 * (size_t)d * sizeof(double), cudaMemcpyHostToDevice, s));
-        dp = (const double *)W->params.p;
+        // host parameters: staged in the pinned buffer after the result record and
+        // read there by the setup kernel (the buffer is mapped into the device's
+        // address space), else copied to the device
+        ST(ensure_host(W, 256 + 2 * (size_t)d * sizeof(double)));
+        double *hp = (double *)((char *)W->h_pinned + 256);
+        memcpy(hp, params, 2 * (size_t)d * sizeof(double));
+        void *dpp = nullptr;
+        if (cudaHostGetDevicePointer(&dpp, hp, 0) != cudaSuccess) {
+            cudaGetLastError();
+            CK(cudaMemcpyAsync(W->params.p, params, 2 * (size_t)d * sizeof(double), cudaMemcpyHostToDevice, s));
+            dpp = W->params.p;
+        }
+        dp = (const double *)dpp;
     }
     // the result record goes straight to the pinned host buffer, mapped into
     // the device's address space: no separate copy back
