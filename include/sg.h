@@ -94,8 +94,8 @@ typedef enum {
 typedef enum {
     SG_PREC_FP64 = 0,   /* every step in IEEE double */
     SG_PREC_MIXED = 1,  /* integrand evaluation and per-cluster folds in float;
-                           cross-cluster and cross-chunk sums in double with
-                           Neumaier compensation */
+                           cross-cluster and cross-chunk sums exact in a
+                           128-bit integer window, rounded once to double */
     SG_PREC_FF = 2      /* float-float: tables, folds and the per-point deviation
                            as unevaluated pairs of floats (about 44 bits) on the
                            FP32 pipes; cross-chunk sums in double */

@@ -98,7 +98,8 @@ struct SgPatDev {
 // item sums the group results.  Both sums run in a fixed order.
 #define SG_GROUP 64
 
-// Per-group partial result: compensated pair and absolute sum.
+// Per-group partial result: the group's exact sum as a pair of doubles
+// (s the nearest double, c the rest) and its absolute sum.
 struct alignas(32) SgGroupSlot {
     double s, c, abs, pad;
 };

@@ -22,9 +22,13 @@
 // and accumulates W * D.  Since every non-centre subgrid's weights sum to
 // zero, sum W f = sum W D, and the cancelling signed sum stays small.
 //
-// Reduction is deterministic: each chunk writes one (sum, abs) slot; the
-// warp that completes an item's last chunk (ticket counter) sums that item's
-// slots in chunk order with Neumaier compensation in FP64.
+// Reduction is deterministic: each chunk writes one (sum, abs) slot, the
+// warps that complete a group of slots and then an item's last group
+// (ticket counters) add them exactly in a 128-bit integer window
+// (sg_xsum.h), so no order of additions can change a bit.
+//
+// In FP64 the deviation's polynomials run in 64-bit fixed point on the
+// integer pipes (sg_fixed.h): GB300 issues FP64 at 1/72 of its FP32 rate.
 #include <math.h>
 #include <stdio.h>
 
@@ -547,9 +551,8 @@ __device__ __forceinline__ SgItemVar item_values(const SgItemRole &R, const SgIn
     return V;
 }
 
-// Blocks [0, nbase) compute one integral each: log f(c) as a compensated sum
-// in a fixed order (thread-strided Neumaier sums, combined by fixed trees
-// within and across the block's warps), or the oscillatory centre phase.  A
+// Blocks [0, nbase) compute one integral each: log f(c), or the oscillatory
+// centre phase, as an exact sum in a 128-bit window (see below).  A
 // whole block per integral spreads a long sum over the SM's four FP64
 // units.  The remaining blocks fill table entries.
 __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase) {

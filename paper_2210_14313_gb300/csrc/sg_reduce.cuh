@@ -133,8 +133,8 @@ __device__ inline void reduce_groups(const SgGroupSlot *g, unsigned long long n,
 
 // Called by the warp that wrote chunk c's slot.  Two-level ticketing: the
 // last chunk of a group reduces the group, the last group reduces the item
-// and calls finish(T, AB) on lane 0 with the item's compensated sum T and its
-// sum of absolute values AB.
+// and calls finish(T, AB) on lane 0 with the item's sum T (the double pair
+// of the exact sum, added) and its sum of absolute values AB.
 template <typename Finish>
 __device__ inline void complete_chunk(const SgFoldArgs &A, int item, unsigned long long c, int lane,
                                       Finish finish) {
