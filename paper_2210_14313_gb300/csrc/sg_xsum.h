@@ -5,7 +5,7 @@
 // the largest biased exponent among them: a term with exponent e becomes its
 // 53-bit significand shifted by e - E + SG_XG (<= SG_XG) bits, truncated
 // towards zero below the unit (at most 2^-(SG_XG + 52) of the largest term,
-// the same for every order of summation).  Up to 2^17 terms then add
+// the same for every order of summation).  Up to 2^22 terms then add
 // exactly as two's complement 128-bit integers, so the sum does not depend
 // on the order of the additions at all, and it is rounded to a double pair
 // (s, c) only once at the end (s the nearest double to the sum, c the
@@ -20,7 +20,7 @@
 #define SG_XS static inline
 #endif
 
-#define SG_XG 56  // guard bits below the largest term's unit in the last place
+#define SG_XG 52  // guard bits below the largest term's unit in the last place
 
 struct SgX {
     unsigned long long lo, hi;  // two's complement, value = hi 2^64 + lo
