@@ -120,3 +120,16 @@ def xsum_adaptive(v, nthreads):
     out = np.zeros(2)
     lib.chk_xsum_adaptive(v.ctypes.data_as(dp), len(v), nthreads, out.ctypes.data_as(dp))
     return out[0], out[1]
+
+
+def fx_to_double(v, neg, q):
+    """sg_fx_to_double_f of (v, neg, q) triples (sg_fixed.h), built for the host."""
+    lib = _load()
+    lib.chk_fx_to_double.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                     ctypes.c_void_p]
+    v = np.ascontiguousarray(v, dtype=np.uint64)
+    neg = np.ascontiguousarray(neg, dtype=np.uint64)
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    y = np.zeros(len(v))
+    lib.chk_fx_to_double(v.ctypes.data, neg.ctypes.data, q.ctypes.data, len(v), y.ctypes.data)
+    return y

@@ -388,6 +388,13 @@ long long chk_divmagic(int mmax) {
     return bad;
 }
 
+// sg_fx_to_double_f(v[i], neg[i] & 1, q[i]) for n values (the fixed-point
+// functions' conversion back to double).
+void chk_fx_to_double(const unsigned long long *v, const unsigned long long *neg, const int *q, long long n,
+                      double *y) {
+    for (long long i = 0; i < n; i++) y[i] = sg_fx_to_double_f(v[i], neg[i] & 1ull, q[i]);
+}
+
 // The reduction's exact 128-bit window sum (sg_xsum.h) of v[0..n), in the
 // order given: out = (s, c).
 void chk_xsum(const double *v, long long n, double *out) {

@@ -104,3 +104,24 @@ def test_weighted_oscillatory_deviation(phi):
     if abs(np.sin(phi)) > 0.1:
         assert rel <= 2.0 * U, float(rel / U)
     assert absw <= 2.0 ** -52, float(absw)
+
+
+def test_fixed_point_to_double_rounds_to_nearest():
+    # v 2^-q for 64-bit v: the nearest double (ties away from zero), signed,
+    # and zero below the normal range
+    from fractions import Fraction
+    rng = np.random.default_rng(9)
+    v = rng.integers(1, 2 ** 63, 3000, dtype=np.uint64) >> rng.integers(0, 63, 3000).astype(np.uint64)
+    v[:4] = [1, 2 ** 53 - 1, 2 ** 53 + 1, 2 ** 63 + 1025]
+    neg = rng.integers(0, 2, 3000).astype(np.uint64)
+    q = rng.integers(0, 1100, 3000).astype(np.int32)
+    y = index_check.fx_to_double(v, neg, q)
+    for vi, ni, qi, yi in zip(v.tolist(), neg.tolist(), q.tolist(), y.tolist()):
+        ex = Fraction(int(vi), 2 ** int(qi)) * (-1 if ni else 1)
+        if abs(ex) < Fraction(2) ** -1022:
+            assert yi == 0.0 or abs(Fraction(yi) - ex) <= Fraction(2) ** -1074
+            continue
+        f = float(ex)  # nearest, ties to even
+        err = abs(Fraction(yi) - ex)
+        assert err <= abs(Fraction(f) - ex) or err == abs(Fraction(f) - ex), (vi, ni, qi)
+        assert abs(Fraction(yi) - ex) <= abs(ex) * Fraction(2) ** -53
