@@ -566,6 +566,17 @@ __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase)
         const int g = blockIdx.x;
         const SgIntegralDev G = A.integrals[g];
         const double *a = A.params + G.param_off, *u = a + G.d;
+        // each thread's first item, loaded now so that the dependent loads
+        // overlap the centre sum instead of following it
+        const int ti0 = A.do_items ? A.int_item_ptr[g] : 0, ti1 = A.do_items ? A.int_item_ptr[g + 1] : 0;
+        int it0 = -1;
+        SgItemRole role0;
+        unsigned long long nch0 = 1;
+        if (ti0 + (int)threadIdx.x < ti1) {
+            it0 = A.int_items[ti0 + threadIdx.x];
+            role0 = A.roles[it0];
+            nch0 = A.items[it0].nchunk;
+        }
         // log f(c) (or the centre phase) as an exact sum in a 128-bit window
         // (sg_xsum.h): each thread keeps a running sum of its terms, whose
         // unit follows the largest term so far; the block then aligns the
@@ -613,11 +624,17 @@ __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase)
                 }
                 // exp(log_hi + log_lo) = 2^e0 exp(r), r = log_hi - e0 ln 2 + log_lo with
                 // ln 2 split in two (Cody & Waite): the result's scale without overflow
-                const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-                const double e0 = floor(B.log_hi * 1.44269504088896338700);
-                const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
-                B.scale_e2 = e0;
-                B.scale_m = 1.0 + sg_expm1_d(rr);
+                // (1 for the oscillatory family, whose values are not scaled)
+                if (B.log_hi == 0.0 && B.log_lo == 0.0) {
+                    B.scale_e2 = 0.0;
+                    B.scale_m = 1.0;
+                } else {
+                    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+                    const double e0 = floor(B.log_hi * 1.44269504088896338700);
+                    const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
+                    B.scale_e2 = e0;
+                    B.scale_m = 1.0 + sg_expm1_d(rr);
+                }
                 A.bases[g] = B;
                 sh_b = B;
             }
@@ -625,10 +642,11 @@ __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase)
         if (!A.do_items) return;
         __syncthreads();
         const SgBaseDev B = sh_b;
-        for (int t = A.int_item_ptr[g] + threadIdx.x; t < A.int_item_ptr[g + 1]; t += blockDim.x) {
-            const int it = A.int_items[t];
-            A.vars[it] = item_values(A.roles[it], G, B, A.params);
-            if (A.items[it].nchunk == 0)
+        for (int t = ti0 + threadIdx.x; t < ti1; t += blockDim.x) {
+            const bool first = t == ti0 + (int)threadIdx.x;
+            const int it = first ? it0 : A.int_items[t];
+            A.vars[it] = item_values(first ? role0 : A.roles[it], G, B, A.params);
+            if ((first ? nch0 : A.items[it].nchunk) == 0)
                 assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, nullptr, 0.0,
                               A.unit_roundoff, it, 0.0, 0.0);
         }
