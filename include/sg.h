@@ -104,7 +104,10 @@ typedef enum {
 /* Which algebraic form of the same Smolyak sum the kernels enumerate.  All
  * three give Q_d^q f up to rounding. */
 typedef enum {
-    SG_FORM_AUTO = 0,        /* SG_FORM_TELESCOPED */
+    SG_FORM_AUTO = 0,        /* SG_FORM_COMBINATION for Gauss-Legendre in FP64 when every
+                                coefficient C(d-1, L-k) is at most 1024 (the difference
+                                forms evaluate several times n_d^q points for a rule
+                                that is not nested), else SG_FORM_TELESCOPED */
     SG_FORM_DIFFERENCE = 1,  /* sum_{|k|<=L} of tensor products of difference rules (Eq. 2.9) */
     SG_FORM_TELESCOPED = 2,  /* difference rules in all but the last active direction;
                                 the last direction folds J^{M+1} - J^1 at once (Alg. 3.1) */
@@ -169,7 +172,8 @@ SG_API sg_status sg_rule_nodes(sg_rule rule, int level, double *x, double *w, in
  * n_d^q = sum over the multi-indices of Eq. 2.6 of prod_i n_{l_i}: the point
  * count with repetition, the unit of the points/s metric.  Also the number
  * of integrand deviations the kernels evaluate for `form` (evals may be
- * NULL).  Errors: SG_EINVAL, SG_ERANGE (count beyond 2^64).
+ * NULL; SG_FORM_AUTO is resolved as for SG_PREC_FP64).
+ * Errors: SG_EINVAL, SG_ERANGE (count beyond 2^64).
  */
 SG_API sg_status sg_count_points(sg_rule rule, int d, int q, sg_form form, uint64_t *points,
                           uint64_t *evals);

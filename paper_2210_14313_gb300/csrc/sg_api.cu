@@ -654,14 +654,31 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
 // entry points
 // ---------------------------------------------------------------------------
 
+// The form SG_FORM_AUTO stands for.  For a rule that is not nested
+// (Gauss-Legendre) the difference forms evaluate the union of two node sets
+// per active direction, several times the n_d^q points of Eq. 2.6, while the
+// combination form evaluates exactly n_d^q; its price is the binomial
+// coefficients C(d-1, L-k), which multiply the rounding errors of the
+// subgrid sums.  In FP64, with every coefficient at most 1024 (for example
+// d = 12, L = 6: at most C(11, 5) = 462), the combination form keeps far
+// below 1e-12 and takes it; everywhere else the telescoped form.
+static sg_form auto_form(sg_rule rule, int d, int L, int prec) {
+    if (prec == SG_PREC_FP64 && (rule->kind & ~SG_KIND_SLOW) == SG_RULE_GAUSS_LEGENDRE && L >= 1) {
+        unsigned __int128 cmax = 0;
+        for (int j = 0; j <= L && j <= d - 1; j++) cmax = std::max(cmax, binom128(d - 1, j));
+        if (cmax <= 1024) return SG_FORM_COMBINATION;
+    }
+    return SG_FORM_TELESCOPED;
+}
+
 static sg_status check_one(sg_rule rule, sg_family fam, int d, int q, sg_precision prec,
                            sg_form *form) {
     if (!rule) return SG_EINVAL;
     if ((int)fam < 0 || (int)fam > 4) return SG_EINVAL;
     if (!prec_ok(prec)) return SG_EINVAL;
     if ((int)*form < 0 || (int)*form > 3) return SG_EINVAL;
-    if (*form == SG_FORM_AUTO) *form = SG_FORM_TELESCOPED;
     if (d < 1 || q < d) return SG_EINVAL;
+    if (*form == SG_FORM_AUTO) *form = auto_form(rule, d, q - d, prec);
     if (d > SG_MAX_D) return SG_ERANGE;
     const int L = q - d;
     if (L > SG_MAX_L || L + 1 > rule->max_level) return SG_ERANGE;
@@ -686,8 +703,8 @@ extern "C" sg_status sg_count_points(sg_rule rule, int d, int q, sg_form form, u
                                      uint64_t *evals) {
     if (!rule || !points) return SG_EINVAL;
     if ((int)form < 0 || (int)form > 3) return SG_EINVAL;
-    if (form == SG_FORM_AUTO) form = SG_FORM_TELESCOPED;
     if (d < 1 || q < d) return SG_EINVAL;
+    if (form == SG_FORM_AUTO) form = auto_form(rule, d, q - d, SG_PREC_FP64);
     if (d > SG_MAX_D) return SG_ERANGE;
     const int L = q - d;
     if (L > SG_MAX_L || L + 1 > rule->max_level) return SG_ERANGE;
@@ -832,7 +849,8 @@ extern "C" sg_status sg_integrate_user(sg_rule rule, sg_integrand f, const doubl
     return SG_OK;
 }
 
-static sg_status batch_reqs(const sg_item *items, int n, std::vector<Req> &reqs, size_t *pool) {
+static sg_status batch_reqs(const sg_item *items, int n, sg_precision prec, std::vector<Req> &reqs,
+                            size_t *pool) {
     if (!items || n < 1) return SG_EINVAL;
     if (n > 65536) return SG_ERANGE;
     reqs.resize(n);
@@ -840,7 +858,7 @@ static sg_status batch_reqs(const sg_item *items, int n, std::vector<Req> &reqs,
     size_t need = 0;
     for (int k = 0; k < n; k++) {
         sg_form f = SG_FORM_AUTO;
-        ST(check_one(items[k].rule, items[k].fam, items[k].d, items[k].q, SG_PREC_FP64, &f));
+        ST(check_one(items[k].rule, items[k].fam, items[k].d, items[k].q, prec, &f));
         reqs[k] = Req{items[k].rule, (int)items[k].fam, items[k].d, items[k].q - items[k].d, (int)f,
                       (long long)items[k].param_offset, 0};
         need = std::max(need, (size_t)items[k].param_offset + 2 * (size_t)items[k].d);
@@ -858,7 +876,7 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     if (prec != SG_PREC_MIXED) guard_tol = 0.0;
     std::vector<Req> reqs;
     size_t pool = 0;
-    ST(batch_reqs(items, n, reqs, &pool));
+    ST(batch_reqs(items, n, prec, reqs, &pool));
     std::lock_guard<std::mutex> lk(g_mu);
     cudaGetLastError();  // a failed earlier call must not surface here
     DevCtx *C = nullptr;
@@ -919,7 +937,7 @@ extern "C" sg_status sg_integrate_grad(sg_rule rule, sg_family fam, const double
                                        void *stream, sg_result *out, double *dparams,
                                        int dparams_on_device) {
     if (!params || !out || !dparams) return SG_EINVAL;
-    sg_form form = SG_FORM_AUTO;
+    sg_form form = SG_FORM_TELESCOPED;  // the adjoint items follow the telescoped form
     ST(check_one(rule, fam, d, q, prec, &form));
     std::lock_guard<std::mutex> lk(g_mu);
     cudaGetLastError();  // a failed earlier call must not surface here

@@ -19,10 +19,13 @@
 // Set-up: the first call on a device (with that device current) looks up the
 // array's device address with cudaGetSymbolAddress and copies the binomial
 // table into it with a synchronous cudaMemcpy; make that first call before
-// any stream capture.  Every call shares the one array and leaves its
-// contents behind; the tickets are cleared at the start of every call.
-// Calls whose work overlaps on the GPU (different streams, or different
-// host threads) race on the array: serialise them.
+// any stream capture.  After that a call copies nothing from host memory:
+// its plan (rule nodes, pattern records) travels as the parameter block of
+// a one-CTA upload kernel, which writes it into the array and clears the
+// tickets in stream order, so the host stack that held the plan may be gone
+// by the time the kernel runs.  Every call shares the one array and leaves
+// its contents behind.  Calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on the array: serialise them.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -114,7 +117,9 @@ sg_status na_setup(int dev, NaDevice **out) {
     return SG_OK;
 }
 
-// Host plan of one integral in the telescoped form, on the stack.
+// Host plan of one integral in the telescoped form, on the stack.  It is
+// passed by value as the upload kernel's parameter block (below the 32 KB
+// limit of kernel parameters).
 struct NaPlan {
     double2 xw[kNaMaxNodes];
     int nxw = 0;
@@ -325,7 +330,33 @@ sg_status na_plan(int kind, int fam, int d, int L, int prec, long long resident_
     return SG_OK;
 }
 
+static_assert(sizeof(NaPlan) <= 32000, "the plan must fit the kernel parameter block");
+
+// Copies n bytes (a multiple of 4) with the CTA's threads.
+__device__ __forceinline__ void na_copy(unsigned char *dst, const void *src, size_t n) {
+    const unsigned *s4 = (const unsigned *)src;
+    unsigned *d4 = (unsigned *)dst;
+    for (size_t i = threadIdx.x; i < n / 4; i += blockDim.x) d4[i] = s4[i];
+}
+
 }  // namespace
+
+// Writes a call's plan into the static array and clears the work counter and
+// tickets.  One CTA; the plan arrives in the kernel's parameter block.
+__global__ void __launch_bounds__(256) sg_na_upload_kernel(const NaPlan P, unsigned char *S) {
+    na_copy(S + kOffXw, P.xw, sizeof(double2) * (P.nxw > 0 ? P.nxw : 1));
+    na_copy(S + kOffInt, &P.integral, sizeof(SgIntegralDev));
+    na_copy(S + kOffBlk, P.blocks, sizeof(SgBlockDev) * P.nblocks);
+    na_copy(S + kOffBe, P.block_end, sizeof(long long) * P.nblocks);
+    na_copy(S + kOffItem, &P.item, sizeof(SgItemDev));
+    na_copy(S + kOffRole, &P.role, sizeof(SgItemRole));
+    na_copy(S + kOffII, &P.item_integral, sizeof(int));
+    const int npat = P.npat > 0 ? P.npat : 1;
+    na_copy(S + kOffPat, P.pats, sizeof(SgPatDev) * npat);
+    na_copy(S + kOffPc, P.pat_chunk0, sizeof(unsigned long long) * npat);
+    unsigned *cnt = (unsigned *)(S + kOffCnt);
+    for (size_t i = threadIdx.x; i < kCntBytes / 4; i += blockDim.x) cnt[i] = 0u;
+}
 
 extern "C" sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, const double *d_params,
                                           int d, int q, sg_precision prec, void *stream,
@@ -342,7 +373,6 @@ extern "C" sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, cons
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return SG_ECUDA;
     std::lock_guard<std::mutex> lk(g_na_mu);
-    cudaGetLastError();  // an earlier failure elsewhere must not surface here
     NaDevice *D = nullptr;
     sg_status st = na_setup(dev, &D);
     if (st != SG_OK) return st;
@@ -357,17 +387,8 @@ extern "C" sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, cons
     do {                                                \
         if ((call) != cudaSuccess) return SG_ECUDA;     \
     } while (0)
-    NA_CK(cudaMemcpyAsync(S + kOffXw, P.xw, sizeof(double2) * (P.nxw > 0 ? P.nxw : 1), cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffInt, &P.integral, sizeof(SgIntegralDev), cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffBlk, P.blocks, sizeof(SgBlockDev) * P.nblocks, cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffBe, P.block_end, sizeof(long long) * P.nblocks, cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffItem, &P.item, sizeof(SgItemDev), cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffRole, &P.role, sizeof(SgItemRole), cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffII, &P.item_integral, sizeof(int), cudaMemcpyHostToDevice, s));
-    const int npat = P.npat > 0 ? P.npat : 1;
-    NA_CK(cudaMemcpyAsync(S + kOffPat, P.pats, sizeof(SgPatDev) * npat, cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(S + kOffPc, P.pat_chunk0, sizeof(unsigned long long) * npat, cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemsetAsync(S + kOffCnt, 0, kCntBytes, s));
+    sg_na_upload_kernel<<<1, 256, 0, s>>>(P, S);
+    NA_CK(cudaGetLastError());
 
     SgSetupArgs sa;
     memset(&sa, 0, sizeof(sa));

@@ -76,6 +76,29 @@ def test_mixed_configs(rules, c):
     assert err <= max(20 * r.err_est, 1e-7)  # the estimate is of the right size
 
 
+# Gauss-Legendre integrals in FP64 under SG_FORM_AUTO, which picks the
+# combination form where every coefficient C(d-1, L-k) is at most 1024
+# (fewer evaluations than the difference forms for a rule that is not
+# nested) and the telescoped form elsewhere: both sides of that boundary,
+# every family, against the oracle at the FP64 bar.
+AUTO_GL = [(d, L) for d, L in [(2, 8), (3, 7), (5, 6), (8, 5), (11, 6), (12, 6), (13, 6), (14, 5),
+                               (14, 4), (20, 3), (33, 2), (46, 2), (200, 1), (7, 0)]]
+
+
+@pytest.mark.parametrize("fam", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("dL", AUTO_GL, ids=lambda t: "d%d_L%d" % t)
+def test_fp64_auto_form_gauss_legendre(rules, dL, fam):
+    d, L = dL
+    c = dict(rule=4, fam=fam, d=d, L=L, params=si.item_params(fam, d, 500 + 7 * d + L))
+    r = sg.integrate(rules[4], fam, c["params"], d, d + L, prec=sg.PREC_FP64)
+    assert rel_err(r, oracle_value(c)) <= FP64_TOL
+    pts, ev = sg.count_points(rules[4], d, d + L)
+    assert r.points == pts == oracle.count_points(4, d, L)
+    assert r.evals == ev
+    comb = L >= 1 and max(math.comb(d - 1, j) for j in range(0, min(L, d - 1) + 1)) <= 1024
+    assert (ev <= pts) == comb or L == 0
+
+
 FF_TOL = 1e-9
 
 
