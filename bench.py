@@ -2,10 +2,15 @@
 on one GB300 (or N independent replicas under torchrun).
 
 Workload (default): d = 12, Gauss-Legendre rule (level l has l nodes),
-q = d + 6, Genz oscillatory integrand with seeded parameters, FP64; one step
-= one integral (table setup, item values, the persistent fold kernel and the
-fixed-order reduction).  The metric's unit is n_d^q, the point count of
-Eq. 2.6 with repetition (593,775 here).
+q = d + 6, Genz oscillatory integrand, FP64 -- the single-integral FP64
+configuration the headline metric is quoted on; the other configurations
+(d = 4 Clenshaw-Curtis, the d = 100 and d = 1000 mixed-precision ones, the
+4096-item batch, the d = 1000 gradient) are reported under "extra" or with
+--workload.  One step = R independent integrals of the workload (R = 1024 by
+default, each with its own seeded parameter draw), each a full single-integral
+call (table setup, item values, the persistent fold kernel and the
+deterministic reduction), issued back to back on one stream.  The metric's
+unit is n_d^q, the point count of Eq. 2.6 with repetition (593,775 here).
 
 --impl reference times the CPU oracle (the plain enumeration the tests use
 as ground truth) on the host cores instead.
@@ -63,15 +68,15 @@ def _dist():
 
 def _workload(name):
     import sg_inputs as si
-    if name == "cfg2":
-        return si.cfg2(), 0
-    if name == "cfg3":
-        return si.cfg3(si.FAM_GAUSSIAN), 1
-    if name == "cfg5":
-        return si.cfg5(), 0
-    if name == "cfg1":
-        return si.cfg1(), 0
-    raise SystemExit("unknown workload " + name)
+    table = {"cfg1": (si.cfg1, 0), "cfg2": (si.cfg2, 0), "cfg3": (lambda: si.cfg3(si.FAM_GAUSSIAN), 1),
+             "cfg3peak": (lambda: si.cfg3(si.FAM_PRODUCT_PEAK), 1), "cfg5": (si.cfg5, 0)}
+    if name not in table:
+        raise SystemExit("unknown workload " + name)
+    f, prec = table[name]
+    return f(), prec
+
+
+RULE_NAMES = {1: "trapezoid", 2: "clenshaw_curtis", 3: "gauss_patterson", 4: "gauss_legendre"}
 
 
 class ClockSampler:
@@ -90,7 +95,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -128,19 +133,21 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_rate(c, budget_s=12.0):
-    """Oracle throughput (points/s) on this host, repeated up to a time budget."""
+def _oracle_rate(c, budget_s=12.0, nthreads=0):
+    """Oracle throughput (points/s) on this host over whole integrals,
+    repeated up to a time budget (at least 3): (median rate, runs, seconds)."""
     import oracle
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
-        n += 1
-        if time.perf_counter() - t0 > budget_s or n >= 200:
-            break
-    dt = time.perf_counter() - t0
     pts = oracle.count_points(c["rule"], c["d"], c["L"])
-    return pts * n / dt, n, dt
+    t_start = time.perf_counter()
+    rates = []
+    while True:
+        t0 = time.perf_counter()
+        oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"], nthreads=nthreads)
+        rates.append(pts / (time.perf_counter() - t0))
+        if len(rates) >= 3 and (time.perf_counter() - t_start > budget_s or len(rates) >= 200):
+            break
+    rates.sort()
+    return rates[len(rates) // 2], len(rates), time.perf_counter() - t_start
 
 
 def max_over_ranks(value, dist, device):
@@ -152,6 +159,15 @@ def max_over_ranks(value, dist, device):
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return t.item()
+
+
+def _config(c, pts, evals, per_step, form):
+    return {"workload": c["name"], "d": c["d"], "q": c["d"] + c["L"], "rule": RULE_NAMES[c["rule"]],
+            "family": sg_family_name(c["fam"]), "points_per_integral": pts, "evals_per_integral": evals,
+            "integrals_per_step": per_step, "form": form,
+            "inputs": "seeded parameter draws of the workload, one per integral (draw 0 = the "
+                      "workload's own)",
+            "l2": "flushed between steps (256 MB write); a step's integrals share the L2-resident plan"}
 
 
 def run_reference(args):
@@ -172,26 +188,39 @@ def run_reference(args):
     tot = sum(times)
     cores = os.cpu_count()
     value = pts * len(times) / tot
+    cfg = _config(c, pts, pts, 1, "difference form, every point evaluated from the full d-vector")
+    cfg["l2"] = "n/a (CPU)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": c["name"], "d": c["d"], "q": c["d"] + c["L"], "rule": "gauss_legendre"
-                   if c["rule"] == 4 else "clenshaw_curtis", "points_per_integral": pts,
-                   "l2": "n/a (CPU)"},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d whole integrals of the workload" % len(times)},
+                         "sample": "one whole integral of the workload per step (draw 0)"},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
+def _fold_roofline(sg, prec, kind, pts, evals, fold_ms, launches):
+    """Roofline of the fold kernel: effective points (the metric's unit) and
+    evaluations per second against the measured per-point ceiling."""
+    fold_avg_s = fold_ms * 1e-3 / max(launches, 1)
+    peak = sg.ceiling(prec, kind)
+    return {"bound": "alu", "achieved": pts / fold_avg_s / 1e9, "peak": peak / 1e9, "unit": "Gpoints/s",
+            "frac": pts / fold_avg_s / peak, "achieved_evals": evals / fold_avg_s / 1e9,
+            "frac_evals": evals / fold_avg_s / peak, "fold_us": fold_avg_s * 1e6,
+            "peak_source": "measured per-point ceiling kernel (sg_ceiling: the fold's per-point "
+                           "sequence on register-resident data), same run"}
+
+
 def run_gpu(args):
+    import ctypes
     import numpy as np
     import torch
     import paper_2210_14313_gb300 as sg
     import oracle
+    import sg_inputs as si
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -204,124 +233,186 @@ def run_gpu(args):
         prec = {"fp64": 0, "mixed": 1, "ff": 2}[args.prec]
     d, L = c["d"], c["L"]
     q = d + L
+    R = args.per_step
     rule = sg.Rule(c["rule"], max_level=L + 1)
     pts, evals = sg.count_points(rule, d, q)
+    lib = sg.load()
     stream = torch.cuda.current_stream()
-    dparams = torch.tensor(c["params"], dtype=torch.float64, device="cuda")
-    dout = torch.zeros(sg.DEV_RESULT_DOUBLES, dtype=torch.float64, device="cuda")
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    hpar = np.stack([si.redraw(c, j) for j in range(R)])
+    dparams = torch.tensor(hpar, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((R, sg.DEV_RESULT_DOUBLES), dtype=torch.float64, device="cuda")
+    calls = [(rule.handle, c["fam"], ctypes.c_void_p(dparams[j].data_ptr()), d, q, prec, sg.FORM_AUTO, sh,
+              ctypes.c_void_p(dout[j].data_ptr())) for j in range(R)]
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     def step():
-        sg.integrate_async(rule, c["fam"], dparams, d, q, dout, prec=prec)
+        f = lib.sg_integrate_async
+        for a in calls:
+            if f(*a) != 0:
+                raise RuntimeError("sg_integrate_async failed")
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    # accuracy of the timed configuration against the oracle
-    ref = oracle.integrate(c["rule"], c["fam"], c["params"], d, L)
+    # accuracy of the timed configuration against the oracle (the first draws)
     got = dout.cpu().numpy()
-    rel_err = abs(got[0] * 2.0 ** (got[1] - ref.exp2) - ref.mant) / abs(ref.mant)
+    errs = []
+    for j in range(min(R, 4)):
+        ref = oracle.integrate(c["rule"], c["fam"], hpar[j], d, L)
+        errs.append(abs(got[j, 0] * 2.0 ** (got[j, 1] - ref.exp2) - ref.mant) / abs(ref.mant))
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.2)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sg.profile_begin(stream)
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
         step()
         ends[k].record(stream)
     torch.cuda.synchronize()
-    fold_ms, fold_launches = sg.profile_end(stream)
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # the fold kernel's own device time, from events around each fold launch
+    # of one more step (outside the timed region: the events sit between the
+    # setup and fold launches)
+    flush.fill_(-1.0)
+    sg.profile_begin(stream)
+    step()
+    fold_ms, fold_launches = sg.profile_end(stream)
+    ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
     tot_ms = max_over_ranks(sum(ms), dist, torch.device("cuda", local))
-    value = ws * pts * args.steps / (tot_ms * 1e-3)
+    value = ws * R * pts * args.steps / (tot_ms * 1e-3)
 
-    # end to end through the public blocking call, host buffers (pinned)
-    hparams = torch.tensor(c["params"], dtype=torch.float64).pin_memory()
-    hp = hparams.numpy()
-    for _ in range(3):
-        sg.integrate(rule, c["fam"], hp, d, q, prec=prec)
+    # end to end through the public blocking call, host buffers (pinned):
+    # parameters from host memory, the result record read back on the host
+    hp = torch.tensor(hpar, dtype=torch.float64).pin_memory().numpy()
+    for j in range(min(R, 8)):
+        sg.integrate(rule, c["fam"], hp[j], d, q, prec=prec)
     torch.cuda.synchronize()
+    ne = max(1, min(args.steps, 5))
     t0 = time.perf_counter()
-    ne = max(args.steps, 5)
     for _ in range(ne):
-        sg.integrate(rule, c["fam"], hp, d, q, prec=prec)
-    e2e_s = (time.perf_counter() - t0) / ne
-    e2e = {"value": ws * pts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(hparams.numel() * 8),
-           "d2h_bytes_per_step": 56, "s_per_integral": e2e_s}
+        for j in range(R):
+            sg.integrate(rule, c["fam"], hp[j], d, q, prec=prec)
+    e2e_s = (time.perf_counter() - t0) / (ne * R)
+    e2e = {"value": ws * pts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(R * 2 * d * 8),
+           "d2h_bytes_per_step": int(R * 7 * 8), "s_per_integral": e2e_s,
+           "how": "sg_integrate (blocking) per integral, host parameters in pinned memory, "
+                  "result record read on the host; %d steps" % ne}
 
-    # roofline of the fold kernel against the measured per-point ceiling
-    fold_avg_s = fold_ms * 1e-3 / max(fold_launches, 1)
-    achieved = evals / fold_avg_s
     kind = 1 if c["fam"] == 1 else 0
-    peak = sg.ceiling(prec, kind)
-    fma_peak = sg.ceiling(prec, 2)
-
+    roof = _fold_roofline(sg, prec, kind, pts, evals, fold_ms, fold_launches)
+    roof["traffic"] = _fold_traffic(c["name"], prec)
+    roof["fma_peak_tflops"] = sg.ceiling(prec, 2) / 1e12
+    form = "combination (Eq. 2.6)" if evals < pts else "telescoped difference form"
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f64", 1: "f32-eval/f64-sum", 2: "f32x2-eval/f64-sum"}[prec],
         "data": "synthetic (seeded SplitMix64 parameters)",
-        "config": {"workload": c["name"], "d": d, "q": q,
-                   "rule": {1: "trapezoid", 2: "clenshaw_curtis", 4: "gauss_legendre"}[c["rule"]],
-                   "family": sg_family_name(c["fam"]), "points_per_integral": pts,
-                   "evals_per_integral": evals, "form": "telescoped",
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "flushed between steps (256 MB write)",
-                   "rel_err_vs_oracle": rel_err},
-        "s_per_integral": tot_ms * 1e-3 / args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gevals/s",
-                     "frac": achieved / peak, "traffic": _fold_traffic(c["name"], prec),
-                     "peak_source": "measured per-point ceiling kernel (sg_ceiling), same run",
-                     "fma_peak_tflops": fma_peak / 1e12},
+        "config": _config(c, pts, evals, R, form),
+        "s_per_integral": tot_ms * 1e-3 / (args.steps * R),
+        "rel_err_vs_oracle": max(errs), "oracle_checked_integrals": len(errs),
+        "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,  # setup + fold per integral
+        "gpu_launches": 2 * R * args.steps,  # setup + fold per integral
         "clocks": clk,
     }
+    line["config"]["parallelism"] = "replicas" if ws > 1 else "single"
+    if clk.get("sm_mhz"):
+        line["clocks"]["ms_per_step_x_mhz"] = line["ms_per_step"] * clk["sm_mhz"]
     if rank == 0 and ws == 1 and not args.no_extra:
-        line["extra"] = _extras(sg, oracle, torch)
+        line["extra"] = _extras(sg, oracle, torch, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         oracle.build()
-        rate, n, dt = _oracle_rate(c)
-        line["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": "%d whole integrals in %.1f s" % (n, dt)}
+        rate, n, dt = _oracle_rate(c, budget_s=8.0)
+        rate1, n1, dt1 = _oracle_rate(c, budget_s=8.0, nthreads=1)
+        line["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "median of %d whole integrals (draw 0) in %.1f s, all cores" % (n, dt),
+                                "one_thread": {"value": rate1, "cores": 1,
+                                               "sample": "median of %d whole integrals in %.1f s" % (n1, dt1)}}
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
-def _extras(sg, oracle, torch):
-    """Precision ladder on every configuration and a batch subset (one GPU):
-    seconds per integral and relative error against the oracle."""
+def _rel(r, o):
+    return abs(r.mant * 2.0 ** (r.exp2 - o.exp2) - o.mant) / abs(o.mant)
+
+
+def _extras(sg, oracle, torch, args):
+    """The other configurations on one GPU: the precision ladder with the
+    fold's roofline, the gradient of the d = 1000 configuration, the batched
+    form of the headline workload, and a subset of the 4096-item batch."""
     import numpy as np
     import sg_inputs as si
     rules = {k: sg.Rule(k, max_level=8) for k in (2, 4)}
     out = {"configs": {}, "batch": {}}
     names = {0: "fp64", 1: "mixed", 2: "ff"}
+    stream = torch.cuda.current_stream()
     for c in [si.cfg1(), si.cfg2(), si.cfg3(si.FAM_PRODUCT_PEAK), si.cfg3(si.FAM_GAUSSIAN), si.cfg5()]:
         ref = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
+        rule = rules[c["rule"]]
         row = {"points": oracle.count_points(c["rule"], c["d"], c["L"])}
         for prec in (0, 1, 2):
+            for _ in range(3):
+                sg.integrate(rule, c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec)
             ts = []
-            for _ in range(7):
-                r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec)
+            sg.profile_begin(stream)
+            for _ in range(21):
+                r = sg.integrate(rule, c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec)
                 ts.append(r.seconds)
-            t = sorted(ts)[3]
-            err = abs(r.mant * 2.0 ** (r.exp2 - ref.exp2) - ref.mant) / abs(ref.mant)
-            row[names[prec]] = {"s_per_integral": t, "points_per_s": row["points"] / t, "rel_err": err,
-                                "err_est": r.err_est}
+            fold_ms, nl = sg.profile_end(stream)
+            t = sorted(ts)[10]
+            rr = _fold_roofline(sg, prec, 1 if c["fam"] == 1 else 0, r.points, r.evals, fold_ms, nl)
+            row[names[prec]] = {"s_per_integral": t, "points_per_s": row["points"] / t, "rel_err": _rel(r, ref),
+                                "err_est": r.err_est, "evals": r.evals,
+                                "roofline": {k: rr[k] for k in ("achieved", "peak", "frac", "frac_evals",
+                                                                "fold_us")}}
         out["configs"][c["name"]] = row
+    # the d = 1000 configuration with its gradient (2000 entries): forward
+    # sum plus the adjoint sub-sums and the assembly kernel, through the
+    # blocking call with host buffers
+    c = si.cfg5()
+    q = c["d"] + c["L"]
+    for prec in (0, 1):
+        for _ in range(2):
+            sg.integrate_grad(rules[2], c["fam"], c["params"], c["d"], q, prec=prec)
+        ts, walls = [], []
+        for _ in range(7):
+            t0 = time.perf_counter()
+            r, g = sg.integrate_grad(rules[2], c["fam"], c["params"], c["d"], q, prec=prec)
+            walls.append(time.perf_counter() - t0)
+            ts.append(r.seconds)
+        t, w = sorted(ts)[3], sorted(walls)[3]
+        out["configs"].setdefault("cfg5_gradient", {})[names[prec]] = {
+            "s_per_call": t, "s_per_call_wall": w, "points": r.points, "evals_incl_adjoint": r.evals,
+            "evals_per_s": r.evals / t, "gradient_entries": int(g.size)}
+    # the headline workload in the batched form: R draws in one persistent launch
+    c = si.cfg2()
+    R = min(args.per_step, 1024)
+    specs, pool = [], []
+    for j in range(R):
+        specs.append((rules[4], c["fam"], c["d"], c["d"] + c["L"], 2 * c["d"] * j))
+        pool.append(si.redraw(c, j))
+    pool = np.concatenate(pool)
+    for prec in (0, 1):
+        sg.integrate_batch(specs, pool, prec=prec)
+        res = sg.integrate_batch(specs, pool, prec=prec)
+        o = oracle.integrate(c["rule"], c["fam"], pool[:2 * c["d"]], c["d"], c["L"])
+        out["configs"].setdefault("cfg2_batched_%d" % R, {})[names[prec]] = {
+            "s": res[0].seconds, "s_per_integral": res[0].seconds / R,
+            "points_per_s": R * res[0].points / res[0].seconds, "rel_err_draw0": _rel(res[0], o)}
     # batch subset: the first items of the 4096-item workload whose point
     # count stays below 5e9 (so that the FP64 form finishes in seconds)
     items = [it for it in si.batch()[:1200]
@@ -339,12 +430,11 @@ def _extras(sg, oracle, torch):
                              items[k]["L"]) for k in small]
     out["batch"]["items"] = len(items)
     out["batch"]["points"] = pts
-    for label, prec, g in (("fp64", 0, 0.0), ("mixed", 1, 0.0), ("mixed_guard_ff_1e-6", 1, 2.5e-7), ("ff", 2, 0.0)):
+    for label, prec, g in (("fp64", 0, 0.0), ("mixed", 1, 0.0), ("mixed_guard_1e-6", 1, 2.5e-7), ("ff", 2, 0.0)):
         sg.integrate_batch(specs, pool, prec=prec, guard_tol=g)
         res = sg.integrate_batch(specs, pool, prec=prec, guard_tol=g)
         t = res[0].seconds
-        errs = [abs(res[k].mant * 2.0 ** (res[k].exp2 - o.exp2) - o.mant) / abs(o.mant)
-                for k, o in zip(small, refs)]
+        errs = [_rel(res[k], o) for k, o in zip(small, refs)]
         out["batch"][label] = {"s": t, "points_per_s": pts / t,
                                "max_rel_err_vs_oracle": max(errs) if errs else None,
                                "oracle_checked_items": len(errs),
@@ -440,8 +530,9 @@ def run_sweep(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--per-step", type=int, default=1024, help="integrals per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2")
     ap.add_argument("--prec", default=None, choices=[None, "fp64", "mixed", "ff"])

@@ -15,6 +15,7 @@
 #include "../../include/sg.h"
 #include "sg_user.h"
 #include "sg_kernels.h"
+#include "sg_lacc.h"
 #include "sg_plan.h"
 #include "sg_rules.h"
 
@@ -374,7 +375,11 @@ struct GraphEntry {
 struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
-    DevBuf tab32, tab64, tabff, slots, gslots, counters, flags, bases, vars, out, vout, grad, params;
+    DevBuf tab32, tab64, tabff, slots, gslots, counters, flags, bases, vars, out, vout, grad, params, lacc;
+    // the first 16 bytes of `counters` (work counter, finished-CTA count and
+    // window flag of single-integral folds) and `lacc` are zero between
+    // calls; false until a fresh allocation has been cleared
+    bool la_clean = false;
     void *h_pinned = nullptr;
     size_t h_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_join = nullptr;
@@ -453,6 +458,7 @@ static sg_status ensure(Workspace *W, DevBuf &b, size_t bytes) {
     }
     b.cap = cap;
     W->epoch++;
+    W->la_clean = false;
     return SG_OK;
 }
 
@@ -483,8 +489,12 @@ static double unit_roundoff(int prec) {
     return prec == 1 ? 5.9604644775390625e-08 : (prec == 2 ? 5.6843418860808015e-14 : 1.1102230246251565e-16);
 }
 
-// Counters: [u64 work][u32 item tickets][u32 group tickets], zeroed per launch.
+// Counters: [u64 work][u32 CTAs finished][u32 window flag][u32 item tickets]
+// [u32 group tickets].
 static size_t counter_bytes(const Plan *P) { return 16 + 4 * (P->items.size() + P->ngroups); }
+
+// The launch's long accumulator of a single-integral fold (sum, absolute sum).
+static const size_t kLaccBytes = (size_t)2 * SG_LA_DIGITS * sizeof(long long);
 
 // Makes every buffer a plan needs large enough (outside any capture).
 static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need64, bool needff,
@@ -502,6 +512,7 @@ static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need6
     ST(ensure(W, W->vout, (size_t)std::max<long long>(P->nv, 1) * sizeof(double)));
     ST(ensure(W, W->grad, (size_t)2 * std::max(P->max_d, 1) * sizeof(double)));
     if (param_doubles) ST(ensure(W, W->params, param_doubles * sizeof(double)));
+    ST(ensure(W, W->lacc, kLaccBytes));
     return SG_OK;
 }
 
@@ -561,12 +572,27 @@ static cudaError_t launch_user_fold(const UserFold &uf, SgFoldArgs &fa, const Pl
     return cudaLaunchKernelExC(&lc, (const void *)uf.kern, args);
 }
 
+// single_ok: the plan may use the single-integral fold (not inside a graph
+// capture, whose replays would not see the host's record of the counters).
 static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *d_params,
-                          double guard_tol, SgOutDev *d_out, cudaStream_t s, const UserFold *uf = nullptr) {
+                          double guard_tol, SgOutDev *d_out, cudaStream_t s, const UserFold *uf = nullptr,
+                          bool single_ok = true) {
     const int prec = P->prec;
     const int nitems = (int)P->items.size();
     SgOutDev *outp = d_out ? d_out : (SgOutDev *)W->out.p;
-    CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
+    // one forward integral: chunk sums go into per-CTA long accumulators and
+    // the counters return to zero at the end of the fold, so no clearing
+    // launch precedes it (except on fresh memory)
+    const bool single = single_ok && !uf && guard_tol == 0.0 && nitems == 1 && P->integrals.size() == 1 &&
+                        P->roles[0].role == SG_ROLE_FORWARD && P->nchunks > 0;
+    if (single) {
+        if (!W->la_clean) {
+            CK(cudaMemsetAsync(W->counters.p, 0, 16, s));
+            CK(cudaMemsetAsync(W->lacc.p, 0, kLaccBytes, s));
+        }
+    } else {
+        CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
+    }
     if (guard_tol > 0.0) CK(cudaMemsetAsync(W->flags.p, 0, 4 * (size_t)nitems, s));
     SgSetupArgs sa;
     memset(&sa, 0, sizeof(sa));
@@ -627,10 +653,14 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     fa.skip_unflagged = nullptr;
     fa.guard_tol = guard_tol;
     fa.unit_roundoff = u;
+    fa.single = single ? 1 : 0;
+    fa.lacc = (long long *)W->lacc.p;
+    fa.cta_done = (unsigned int *)((char *)W->counters.p + 8);
     CK(prof_mark(W, true, s));
     if (uf) CK(launch_user_fold(*uf, fa, P, C, s));
     else CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
     CK(prof_mark(W, false, s));
+    if (single) W->la_clean = true;
     if (prec == 1 && guard_tol > 0.0) {
         // precision guard: recompute flagged items in float-float
         CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
@@ -647,6 +677,8 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
         CK(sg_launch_fold(fa, 2, 0, fold_cfg(P, 2, C), s));
         CK(prof_mark(W, false, s));
     }
+    // leave the counters of the single-integral fold as it expects them
+    if (!single) CK(cudaMemsetAsync(W->counters.p, 0, 16, s));
     return SG_OK;
 }
 
@@ -905,7 +937,7 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     if (it == W->graphs.end()) {
         GraphEntry ge;
         CK(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
-        sg_status st = run_plan(P, W, C, dp, guard_tol, nullptr, g);
+        sg_status st = run_plan(P, W, C, dp, guard_tol, nullptr, g, nullptr, false);
         cudaError_t ce = cudaStreamEndCapture(g, &ge.g);
         if (st != SG_OK) {
             if (ge.g) cudaGraphDestroy(ge.g);

@@ -159,4 +159,15 @@ struct SgFoldArgs {
     const int *skip_unflagged;       // if non-NULL: only items with flags[item] != 0 are run
     double guard_tol;
     double unit_roundoff;            // 2^-24 or 2^-53
+    // Single-integral plans (one forward item, no guard): every chunk's sum
+    // goes into a long accumulator in the CTA's shared memory (sg_lacc.h),
+    // each CTA adds its accumulator into the launch's accumulator `lacc`
+    // (2 SG_LA_DIGITS limbs: the sum, then the absolute sum) and the last
+    // CTA to finish rounds it and assembles the result.  cta_done[0] counts
+    // finished CTAs, cta_done[1] flags a term outside the accumulator's
+    // window; that last CTA returns lacc, both counters and the work counter
+    // to zero.
+    int single;
+    long long *lacc;
+    unsigned int *cta_done;
 };

@@ -38,6 +38,7 @@
 #include "sg_fixed.h"
 #include "sg_fold_logic.h"
 #include "sg_kernels.h"
+#include "sg_lacc.h"
 #include "sg_reduce.cuh"
 
 #define FULL_MASK 0xffffffffu
@@ -455,15 +456,82 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     }
 }
 
+// The value of a long accumulator held one limb per lane, as s + c, by
+// the warp: one carry step brings every limb below 2^53 so that
+// limb * 2^(32 lane + SG_LA_E0) is an exact double, and those 32 doubles are
+// added exactly in a 128-bit window (sg_xsum.h; terms more than 104 bits
+// below the largest are cut towards zero, the same on every run).
+__device__ __forceinline__ void la_warp_round(long long L, int lane, double &s, double &c) {
+    const long long hi = L >> 32;  // arithmetic: floor division by 2^32
+    const long long up = __shfl_up_sync(FULL_MASK, hi, 1);
+    long long v = lane == 31 ? L : (long long)((unsigned long long)L & 0xffffffffull);
+    if (lane > 0) v += up;
+    const double t = ldexp((double)v, 32 * lane + SG_LA_E0);
+    const int E = warp_max_exp(sg_x_exp(t));
+    SgX a = {0ull, 0ull};
+    sg_x_add(a, t, E);
+    warp_xsum(a, E, s, c);
+}
+
+// End of a single-integral fold (SgFoldArgs::single): the CTA adds the
+// non-zero limbs of its long accumulator into the launch's accumulator with
+// integer atomics (the order of the additions cannot change the sum, so the
+// result does not depend on which CTA ran which chunk); the last CTA to
+// finish rounds it, assembles the output record and returns the launch's
+// accumulator and counters to zero for the next launch.
+__device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la, int *s_flag) {
+    const int NL = 2 * SG_LA_DIGITS;
+    __syncthreads();
+    if ((int)threadIdx.x < NL) {
+        const long long v = s_la[threadIdx.x];
+        if (v) atomicAdd((unsigned long long *)&A.lacc[threadIdx.x], (unsigned long long)v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_flag[0]) atomicOr(A.cta_done + 1, 1u);
+        __threadfence();
+        s_flag[1] = atomicAdd(A.cta_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_flag[1] || threadIdx.x >= 32) return;
+    __threadfence();
+    const int lane = threadIdx.x;
+    const long long Ls = __ldcg(A.lacc + lane), La = __ldcg(A.lacc + SG_LA_DIGITS + lane);
+    A.lacc[lane] = 0;
+    A.lacc[SG_LA_DIGITS + lane] = 0;
+    double s, c, as, ac;
+    la_warp_round(Ls, lane, s, c);
+    la_warp_round(La, lane, as, ac);
+    if (lane == 0) {
+        // the item values and the scale come from the setup kernel
+        cudaGridDependencySynchronize();
+        const bool ovf = __ldcg(A.cta_done + 1) != 0u;
+        const double T = ovf ? __longlong_as_double(0x7ff8000000000000ll) : s + c;
+        assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, A.guard_tol,
+                      A.unit_roundoff, 0, T, as + ac);
+        *A.work = 0ull;
+        A.cta_done[0] = 0u;
+        A.cta_done[1] = 0u;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     typedef typename PrefixState<T>::type PS;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_la[2 * SG_LA_DIGITS];
+    __shared__ int s_flag[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     PS *sP = (PS *)smem + (size_t)warp * SG_APAD;
     SgPrefixPos *sPos = (SgPrefixPos *)(smem + (size_t)nw * SG_APAD * sizeof(PS)) + warp * SG_MAX_R;
     int *sIdx = (int *)(smem + (size_t)nw * (SG_APAD * sizeof(PS) + SG_MAX_R * sizeof(SgPrefixPos))) + warp * SG_MAX_R;
     bool waited = false;
+    if (A.single) {
+        if ((int)threadIdx.x < 2 * SG_LA_DIGITS) s_la[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_flag[0] = 0;
+        __syncthreads();
+    }
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(A.work, 1ull);
@@ -497,15 +565,28 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
             acc = warp_sum(std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa));
             aabs = warp_sum((double)F.habs);
         }
+        const double cf = P->coef;  // 1 for most patterns: skip two dependent FP64 steps
+        const double vsum = cf == 1.0 ? acc : acc * cf, vabs = cf == 1.0 ? aabs : aabs * fabs(cf);
+        if (A.single) {
+            // lane k adds digit k of the chunk's sum and absolute sum into the
+            // CTA's long accumulator (at most three lanes of each are non-zero,
+            // and no two lanes share a limb)
+            int ovf = 0;
+            const long long d1 = sg_la_digit(vsum, lane, &ovf), d2 = sg_la_digit(vabs, lane, &ovf);
+            if (d1) atomicAdd((unsigned long long *)&s_la[lane], (unsigned long long)d1);
+            if (d2) atomicAdd((unsigned long long *)&s_la[SG_LA_DIGITS + lane], (unsigned long long)d2);
+            if (ovf) s_flag[0] = 1;
+            continue;
+        }
         if (lane == 0) {
             SgSlot sl;
-            const double cf = P->coef;  // 1 for most patterns: skip two dependent FP64 steps
-            sl.sum = cf == 1.0 ? acc : acc * cf;
-            sl.abs = cf == 1.0 ? aabs : aabs * fabs(cf);
+            sl.sum = vsum;
+            sl.abs = vabs;
             A.slots[c] = sl;
         }
         complete_chunk(A, item, c, lane);
     }
+    if (A.single) finish_single(A, s_la, s_flag);
 }
 
 // Float fold: register budget for 4 CTAs of 8 warps per SM.  Double fold:

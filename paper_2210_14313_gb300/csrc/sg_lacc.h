@@ -1,0 +1,121 @@
+// A long fixed-point accumulator for order-independent sums of doubles: the
+// single-integral fold adds every chunk's sum into one per CTA, and the last
+// CTA adds the CTAs' accumulators, all as integers.
+//
+// A value is sum_k D_k 2^(32k + SG_LA_E0), k = 0 .. SG_LA_DIGITS-1, held as
+// SG_LA_DIGITS signed 64-bit limbs that each collect 32-bit digits: a double
+// enters as its significand cut into 32-bit digits at fixed positions (at
+// most three digits are non-zero), and each digit is added into its limb
+// with one integer addition.  No carry moves between limbs while adding, so
+// the limbs can be updated by independent atomic additions, and up to 2^31
+// terms fit before a limb could overflow.  Integer addition is associative,
+// so the sum is the same for every order and every split of the terms over
+// threads, CTAs or launches; it is rounded once at the end.  The window
+// covers 2^SG_LA_E0 = 2^-576 to 2^448: bits of a term below 2^-576 are cut
+// off (towards zero, the same in every order), terms of magnitude 2^447 or
+// more, infinities and NaNs set the overflow flag instead.
+//
+// This is the classical "long accumulator" of exact dot products
+// (U. Kulisch, "Computer Arithmetic and Validity", de Gruyter 2008) with
+// the carry-save digit layout that lets the parts update independently.
+#pragma once
+
+#include "sg_xsum.h"
+
+#define SG_LA_DIGITS 32
+#define SG_LA_E0 (-576)
+
+// Digit k of v (signed: the digit of |v| with the sign of v); sets *ovf for
+// terms outside the window.
+SG_XS long long sg_la_digit(double v, int k, int *ovf) {
+    const unsigned long long b = sg_xs_bits(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0x7ff) {
+        *ovf = 1;
+        return 0;
+    }
+    const unsigned long long m = (b & 0xfffffffffffffull) | ((unsigned long long)(e != 0) << 52);
+    if (!m) return 0;
+    // |v| = m 2^(s + SG_LA_E0)
+    const int s = (e ? e : 1) - 1075 - SG_LA_E0;
+    if (s + 53 > 32 * SG_LA_DIGITS - 1) {
+        *ovf = 1;
+        return 0;
+    }
+    const int lo = 32 * k - s;  // digit k holds bits lo .. lo + 31 of m
+    unsigned long long dg;
+    if (lo >= 53 || lo <= -32) dg = 0;
+    else if (lo >= 0) dg = (m >> lo) & 0xffffffffull;
+    else dg = (m << -lo) & 0xffffffffull;
+    return (b >> 63) ? -(long long)dg : (long long)dg;
+}
+
+// Index of the lowest digit that can be non-zero for v (its non-zero digits
+// lie in k0 .. k0 + 2), or -1 when v has no bits inside the window; sets
+// *ovf for terms above it, infinities and NaNs.
+SG_XS int sg_la_first_digit(double v, int *ovf) {
+    const unsigned long long b = sg_xs_bits(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0x7ff) {
+        *ovf = 1;
+        return -1;
+    }
+    if (!(b & 0x7fffffffffffffffull)) return -1;
+    const int s = (e ? e : 1) - 1075 - SG_LA_E0;  // lowest bit of the significand
+    if (s + 53 > 32 * SG_LA_DIGITS - 1) {
+        *ovf = 1;
+        return -1;
+    }
+    if (s + 53 <= 0) return -1;
+    return (s < 0 ? 0 : s) >> 5;
+}
+
+// The value of the limbs as s + c (s the double nearest the sum of the top
+// 128 bits of its magnitude, c the double nearest the rest of those bits);
+// the bits below the top 128 are dropped (at most 2^-96 of |sum|).  The
+// limbs are normalised in place on the way (each ends up holding one 32-bit
+// digit of the magnitude), so that the kernels can run this on an array in
+// shared memory without a register copy of it.
+SG_XS void sg_la_round(long long *limb, double *s, double *c) {
+    long long carry = 0;
+#pragma unroll 1
+    for (int k = 0; k < SG_LA_DIGITS; k++) {
+        const long long t = limb[k] + carry;
+        limb[k] = (long long)((unsigned long long)t & 0xffffffffull);
+        carry = t >> 32;  // arithmetic: floor division by 2^32
+    }
+    const int neg = carry < 0;
+    if (neg) {  // two's complement of the digit string
+        unsigned long long cy = 1;
+#pragma unroll 1
+        for (int k = 0; k < SG_LA_DIGITS; k++) {
+            const unsigned long long t = ((~(unsigned long long)limb[k]) & 0xffffffffull) + cy;
+            limb[k] = (long long)(t & 0xffffffffull);
+            cy = t >> 32;
+        }
+    }
+    int h = SG_LA_DIGITS - 1;
+    while (h >= 0 && limb[h] == 0) h--;
+    if (h < 0) {
+        *s = 0.0;
+        *c = 0.0;
+        return;
+    }
+    if (h < 3) h = 3;
+    SgX a;
+    a.hi = ((unsigned long long)limb[h] << 32) | (unsigned long long)limb[h - 1];
+    a.lo = ((unsigned long long)limb[h - 2] << 32) | (unsigned long long)limb[h - 3];
+    // unit of the window: 2^(32 (h - 3) + SG_LA_E0) = 2^(E - 1075 - SG_XG);
+    // a magnitude with the top bit set moves one bit down (sg_x_pair reads
+    // the window as two's complement)
+    int E = 32 * (h - 3) + SG_LA_E0 + 1075 + SG_XG;
+    if (a.hi >> 63) {
+        a.lo = (a.lo >> 1) | (a.hi << 63);
+        a.hi >>= 1;
+        E += 1;
+    }
+    double hs, hc;
+    sg_x_pair(a, E, &hs, &hc);
+    *s = neg ? -hs : hs;
+    *c = neg ? -hc : hc;
+}

@@ -96,39 +96,41 @@ SEED_CFG4 = 0x5EED0004
 SEED_CFG5 = 0x5EED0005
 
 
+def _config(name, rule, fam, d, L, seed, **draw_kw):
+    return dict(name=name, rule=rule, fam=fam, d=d, L=L, seed=seed, draw_kw=draw_kw,
+                params=family_params(fam, d, seed, **draw_kw))
+
+
 def cfg1():
     """d=4, Clenshaw-Curtis, q=d+5, exp-linear with c_i ~ U(0,1)."""
-    d = 4
-    return dict(name="cfg1_d4_cc_L5_explinear", rule=RULE_CLENSHAW_CURTIS,
-                fam=FAM_EXP_LINEAR, d=d, L=5,
-                params=family_params(FAM_EXP_LINEAR, d, SEED_CFG1))
+    return _config("cfg1_d4_cc_L5_explinear", RULE_CLENSHAW_CURTIS, FAM_EXP_LINEAR, 4, 5, SEED_CFG1)
 
 
 def cfg2():
     """d=12, Gauss-Legendre (level i has i nodes), q=d+6, oscillatory,
     a_i ~ U(0,1) rescaled to sum 4.5, u_0 ~ U(0,1)."""
-    d = 12
-    return dict(name="cfg2_d12_gl_L6_oscillatory", rule=RULE_GAUSS_LEGENDRE,
-                fam=FAM_OSCILLATORY, d=d, L=6,
-                params=family_params(FAM_OSCILLATORY, d, SEED_CFG2, sum_a=4.5))
+    return _config("cfg2_d12_gl_L6_oscillatory", RULE_GAUSS_LEGENDRE, FAM_OSCILLATORY, 12, 6, SEED_CFG2,
+                   sum_a=4.5)
 
 
 def cfg3(fam: int = FAM_PRODUCT_PEAK):
     """d=100, Clenshaw-Curtis, q=d+3, product peak or gaussian,
     a_i ~ U(0,1) rescaled to sum 7, u_i ~ U(0,1)."""
-    d = 100
-    name = "cfg3_d100_cc_L3_" + FAMILY_NAMES[fam]
-    return dict(name=name, rule=RULE_CLENSHAW_CURTIS, fam=fam, d=d, L=3,
-                params=family_params(fam, d, SEED_CFG3 + fam, sum_a=7.0))
+    return _config("cfg3_d100_cc_L3_" + FAMILY_NAMES[fam], RULE_CLENSHAW_CURTIS, fam, 100, 3, SEED_CFG3 + fam,
+                   sum_a=7.0)
 
 
 def cfg5():
     """d=1000, Clenshaw-Curtis, q=d+2, gaussian-lin with a_i ~ U(0.5,1.5)/d."""
     d = 1000
-    return dict(name="cfg5_d1000_cc_L2_gaussian_lin", rule=RULE_CLENSHAW_CURTIS,
-                fam=FAM_GAUSSIAN_LIN, d=d, L=2,
-                params=family_params(FAM_GAUSSIAN_LIN, d, SEED_CFG5,
-                                     a_lo=0.5, a_hi=1.5, a_scale=1.0 / d))
+    return _config("cfg5_d1000_cc_L2_gaussian_lin", RULE_CLENSHAW_CURTIS, FAM_GAUSSIAN_LIN, d, 2, SEED_CFG5,
+                   a_lo=0.5, a_hi=1.5, a_scale=1.0 / d)
+
+
+def redraw(c, j: int) -> np.ndarray:
+    """Parameters of draw j of a workload: the same distribution, seed
+    c["seed"] + 2^16 j (draw 0 is the workload's own parameters)."""
+    return family_params(c["fam"], c["d"], c["seed"] + 0x10000 * j, **c["draw_kw"])
 
 
 def item_params(fam: int, d: int, seed: int) -> np.ndarray:

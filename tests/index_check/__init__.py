@@ -133,3 +133,17 @@ def fx_to_double(v, neg, q):
     y = np.zeros(len(v))
     lib.chk_fx_to_double(v.ctypes.data, neg.ctypes.data, q.ctypes.data, len(v), y.ctypes.data)
     return y
+
+
+def lacc(v, nparts=1):
+    """(s, c, overflow) of the single-integral fold's long accumulator
+    (sg_lacc.h) over v, split into nparts parts whose limbs are added."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_lacc.argtypes = [dp, ctypes.c_longlong, ctypes.c_int, dp]
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(4)
+    lib.chk_lacc(v.ctypes.data_as(dp), len(v), nparts, out.ctypes.data_as(dp))
+    if out[3]:
+        raise AssertionError("%d non-zero digits outside the three added per term" % out[3])
+    return out[0], out[1], int(out[2])

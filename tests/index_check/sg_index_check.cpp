@@ -17,6 +17,7 @@
 
 #include "../../paper_2210_14313_gb300/csrc/sg_fixed.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_xsum.h"
+#include "../../paper_2210_14313_gb300/csrc/sg_lacc.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_fold_logic.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_plan.h"
 #include "../../paper_2210_14313_gb300/csrc/sg_rules.h"
@@ -420,6 +421,32 @@ void chk_xsum_adaptive(const double *v, long long n, int nthreads, double *out) 
         sg_x_plus(tot, acc[t]);
     }
     sg_x_pair(tot, Eb, &out[0], &out[1]);
+}
+
+// The single-integral fold's long accumulator (sg_lacc.h): v[0..n) split
+// into nparts contiguous parts (one set of limbs each, as the CTAs hold
+// them), the parts' limbs added, then rounded: out = (s, c, overflow flag,
+// digits outside the three the kernels add).
+void chk_lacc(const double *v, long long n, int nparts, double *out) {
+    std::vector<long long> tot(SG_LA_DIGITS, 0);
+    out[3] = 0;
+    int ovf = 0;
+    for (int p = 0; p < nparts; p++) {
+        std::vector<long long> part(SG_LA_DIGITS, 0);
+        const long long i0 = n * p / nparts, i1 = n * (p + 1) / nparts;
+        for (long long i = i0; i < i1; i++) {
+            // as the kernels add a term: the (at most three) digits from the first
+            const int k0 = sg_la_first_digit(v[i], &ovf);
+            for (int k = 0; k < SG_LA_DIGITS; k++) {
+                const long long dg = sg_la_digit(v[i], k, &ovf);
+                if (dg && (k0 < 0 || k < k0 || k > k0 + 2)) out[3] += 1;  // a digit the kernels would miss
+                if (k0 >= 0 && k >= k0 && k <= k0 + 2) part[k] += dg;
+            }
+        }
+        for (int k = 0; k < SG_LA_DIGITS; k++) tot[k] += part[k];
+    }
+    sg_la_round(tot.data(), &out[0], &out[1]);
+    out[2] = ovf;
 }
 
 }  // extern "C"

@@ -1,6 +1,6 @@
-"""The reduction's exact summation in a 128-bit integer window (sg_xsum.h),
-built for the host: against exact rational sums, independent of the order of
-the terms."""
+"""The reduction's exact summations, built for the host: the 128-bit window
+of sg_xsum.h and the long accumulator of sg_lacc.h, against exact rational
+sums, independent of the order of the terms and of how they are split."""
 from fractions import Fraction
 
 import numpy as np
@@ -62,3 +62,37 @@ def test_adaptive_units_match_the_exact_sum(k, nthreads):
     err = abs(Fraction(s) + Fraction(c) - ex)
     assert err <= Fraction(len(v)) * Fraction(big) * Fraction(2) ** -103
     assert index_check.xsum_adaptive(v, nthreads) == (s, c)
+
+
+def _lacc_cases():
+    rng = np.random.default_rng(5)
+    for v in list(_cases())[:6]:  # the seventh lies wholly below the window (2^-576)
+        yield v
+    yield rng.standard_normal(3000) * 10.0 ** rng.uniform(-150, 130, 3000)   # 280 binades
+    yield np.array([2.0 ** 446, -(2.0 ** 446), 2.0 ** -570, 1.0])             # both window ends
+    yield -rng.uniform(0, 1, 777)                                             # negative sum
+
+
+@pytest.mark.parametrize("k", range(9))
+@pytest.mark.parametrize("nparts", [1, 3, 152])
+def test_long_accumulator_is_exact_and_split_invariant(k, nparts):
+    v = list(_lacc_cases())[k]
+    s, c, ovf = index_check.lacc(v, nparts)
+    assert ovf == 0
+    ex = _exact(v)
+    # the top 128 bits of the sum are kept: s is the nearest double to the
+    # exact sum (none of these cases sits near a tie), s + c within 2^-96
+    assert s == float(ex)
+    assert abs(Fraction(s) + Fraction(c) - ex) <= abs(ex) * Fraction(2) ** -96
+    rng = np.random.default_rng(k)
+    assert index_check.lacc(rng.permutation(v), 7) == (s, c, 0)
+
+
+def test_long_accumulator_window_ends():
+    # below 2^-576 a term is cut towards zero; from 2^447 on it overflows
+    assert index_check.lacc(np.array([1.0, 2.0 ** -600]))[:2] == (1.0, 0.0)
+    assert index_check.lacc(np.array([2.0 ** -570, 2.0 ** -600]))[:2] == (2.0 ** -570, 0.0)
+    assert index_check.lacc(np.array([1.0, 2.0 ** 447]))[2] == 1
+    assert index_check.lacc(np.array([1.0, float("inf")]))[2] == 1
+    assert index_check.lacc(np.array([1.0, float("nan")]))[2] == 1
+    assert index_check.lacc(np.array([0.0, -0.0])) == (0.0, 0.0, 0)
