@@ -104,14 +104,16 @@ typedef enum {
 /* Which algebraic form of the same Smolyak sum the kernels enumerate.  All
  * three give Q_d^q f up to rounding. */
 typedef enum {
-    SG_FORM_AUTO = 0,        /* SG_FORM_COMBINATION for Gauss-Legendre in FP64 when every
-                                coefficient C(d-1, L-k) is at most 1024 (the difference
-                                forms evaluate several times n_d^q points for a rule
-                                that is not nested), else SG_FORM_TELESCOPED */
+    SG_FORM_AUTO = 0,        /* SG_FORM_MERGED (gradients: SG_FORM_TELESCOPED) */
     SG_FORM_DIFFERENCE = 1,  /* sum_{|k|<=L} of tensor products of difference rules (Eq. 2.9) */
     SG_FORM_TELESCOPED = 2,  /* difference rules in all but the last active direction;
                                 the last direction folds J^{M+1} - J^1 at once (Alg. 3.1) */
-    SG_FORM_COMBINATION = 3  /* Eq. 2.6 literally (binomial coefficients) */
+    SG_FORM_COMBINATION = 3, /* Eq. 2.6 literally (binomial coefficients) */
+    SG_FORM_MERGED = 4       /* every distinct point once, with its merged weight (Eq. 2.8):
+                                the difference-form terms of all subgrids that share a point
+                                added into one weight, computed on the host in double-double;
+                                fewest evaluations, and no worse conditioned than the
+                                difference form */
 } sg_form;
 
 typedef struct sg_rule_s *sg_rule;  /* opaque, library-owned */
@@ -121,7 +123,8 @@ typedef struct {
     double mant;       /* 0.5 <= |mant| < 1 (or 0) */
     int64_t exp2;
     double cond;       /* sum_p |W_p D_p| / |sum|: conditioning of the signed sum */
-    double err_est;    /* estimated relative rounding error of the result */
+    double err_est;    /* estimated relative rounding error of the result: 0.05 u cond
+                          (u = 2^-53 FP64, 2^-44 float-float), 0.5 2^-24 cond mixed */
     uint64_t points;   /* n_d^q: points of Eq. 2.6 with repetition (the metric's unit) */
     uint64_t evals;    /* integrand deviations the kernels evaluated */
     double seconds;    /* device time of the call (CUDA events) */
@@ -217,7 +220,10 @@ typedef struct {
  * device memory; item k reads pool[param_offset .. param_offset + 2d).
  * With prec = SG_PREC_MIXED and guard_tol > 0, items whose estimated
  * rounding error exceeds guard_tol are recomputed in float-float
- * (SG_PREC_FF) by a second persistent launch in the same graph.  out: n host records.  Blocking.
+ * (SG_PREC_FF) by a second persistent launch in the same graph, and those whose
+ * float-float estimate still exceeds it by a third one in FP64.  The mixed
+ * estimate is 0.5 * 2^-24 * cond (an upper bound of the float fold's error
+ * over the 4096-integral batch workload).  out: n host records.  Blocking.
  * Limits: 1 <= n <= 65536, per item as sg_integrate.
  */
 SG_API sg_status sg_integrate_batch(const sg_item *items, int n, const double *params_pool,
@@ -348,7 +354,7 @@ SG_API sg_status sg_eval_functions(int kind, sg_precision prec, const double *d_
  * libraries to allocate behind its back.  This entry point takes the rule
  * kind instead of a handle, device params (2d doubles) and a device result
  * record, like sg_integrate_async, and uses the telescoped form.  Its device
- * scratch is one fixed array of about 4.2 MB inside the library, held by
+ * scratch is one fixed array of about 5.2 MB inside the library, held by
  * every GPU that loads the library until the process exits.
  * Rules: the four kinds with standard growth (Gauss-Patterson: q - d <= 5).
  * Limits: 1 <= d <= 1024, 0 <= q - d <= 6, at most 131072 table entries

@@ -23,7 +23,7 @@ RULE_TRAPEZOID, RULE_CLENSHAW_CURTIS, RULE_GAUSS_PATTERSON, RULE_GAUSS_LEGENDRE 
 GROWTH_STANDARD, GROWTH_SLOW = 0, 1
 FAM_EXP_LINEAR, FAM_OSCILLATORY, FAM_PRODUCT_PEAK, FAM_GAUSSIAN, FAM_GAUSSIAN_LIN = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED, PREC_FF = 0, 1, 2
-FORM_AUTO, FORM_DIFFERENCE, FORM_TELESCOPED, FORM_COMBINATION = 0, 1, 2, 3
+FORM_AUTO, FORM_DIFFERENCE, FORM_TELESCOPED, FORM_COMBINATION, FORM_MERGED = 0, 1, 2, 3, 4
 
 SG_OK = 0
 STATUS_NAMES = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ERANGE", 3: "SG_ENOMEM", 4: "SG_ECUDA",

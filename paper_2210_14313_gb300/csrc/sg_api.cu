@@ -116,7 +116,7 @@ extern "C" sg_status sg_rule_init_growth(sg_rule_kind kind, sg_growth growth, in
     }
     std::vector<double> tx(2 * 4097 + 2), tw(2 * 4097 + 2);
     std::vector<double2> all;
-    for (int bk = 0; bk < 3; bk++)
+    for (int bk = 0; bk < 4; bk++)
         for (int k = 1; k < max_level; k++) {
             int n = sg_block(ikind, bk, k, tx.data(), tw.data());
             r->x[bk][k].assign(tx.begin(), tx.begin() + n);
@@ -228,6 +228,8 @@ static sg_status plan_upload(Plan *P, const u64 *d_binom) {
     const size_t o_do = carve<int>(sz, P->delta_off.size() + 1);
     const size_t o_dm = carve<int>(sz, P->delta_m.size() + 1);
     const size_t o_cs = carve<SgChunkStart>(sz, (size_t)P->nchunks);
+    const size_t o_w64 = carve<SgW64>(sz, P->wt64.size());
+    const size_t o_wff = carve<float2>(sz, P->wtff.size());
     std::vector<unsigned char> host(sz, 0);
     memcpy(&host[o_int], P->integrals.data(), P->integrals.size() * sizeof(SgIntegralDev));
     memcpy(&host[o_blk], P->blocks.data(), P->blocks.size() * sizeof(SgBlockDev));
@@ -242,6 +244,10 @@ static sg_status plan_upload(Plan *P, const u64 *d_binom) {
     if (!P->delta_off.empty()) {
         memcpy(&host[o_do], P->delta_off.data(), P->delta_off.size() * sizeof(int));
         memcpy(&host[o_dm], P->delta_m.data(), P->delta_m.size() * sizeof(int));
+    }
+    if (!P->wt64.empty()) {
+        memcpy(&host[o_w64], P->wt64.data(), P->wt64.size() * sizeof(SgW64));
+        memcpy(&host[o_wff], P->wtff.data(), P->wtff.size() * sizeof(float2));
     }
     if (cudaMalloc(&P->dmem, sz) != cudaSuccess) {
         P->dmem = nullptr;
@@ -262,6 +268,8 @@ static sg_status plan_upload(Plan *P, const u64 *d_binom) {
     P->d_delta_off = (int *)(b + o_do);
     P->d_delta_m = (int *)(b + o_dm);
     P->d_delta_xw = P->reqs[0].rule->d_xw;
+    P->d_wt64 = (const SgW64 *)(b + o_w64);
+    P->d_wtff = (const float2 *)(b + o_wff);
     // chunk starts: unranked once per plan on the device (the legacy stream,
     // like the copy above, and waited for, since callers' streams may not
     // synchronise with it)
@@ -484,9 +492,14 @@ static sg_status ensure_host(Workspace *W, size_t bytes) {
         if (s_ != SG_OK) return s_;      \
     } while (0)
 
-// Unit roundoff of a precision (float-float: about 44 significant bits).
+// Effective unit roundoff of a precision: the error estimate of a result is
+// 0.05 * this * cond.  Double: 2^-53; float-float: 2^-44 (about 44
+// significant bits).  The float fold's rounding errors reach 0.33 * 2^-24 *
+// cond (the largest over the 4096 integrals of the batch workload, measured
+// against the separable pin), so its estimate uses 10 * 2^-24: 0.5 * 2^-24 *
+// cond, an upper bound there, which the precision guard relies on.
 static double unit_roundoff(int prec) {
-    return prec == 1 ? 5.9604644775390625e-08 : (prec == 2 ? 5.6843418860808015e-14 : 1.1102230246251565e-16);
+    return prec == 1 ? 5.9604644775390625e-07 : (prec == 2 ? 5.6843418860808015e-14 : 1.1102230246251565e-16);
 }
 
 // Counters: [u64 work][u32 CTAs finished][u32 window flag][u32 item tickets]
@@ -654,6 +667,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     fa.guard_tol = guard_tol;
     fa.unit_roundoff = u;
     fa.single = single ? 1 : 0;
+    fa.wtab = prec == 0 ? (const void *)P->d_wt64 : (const void *)P->d_wtff;
     fa.lacc = (long long *)W->lacc.p;
     fa.cta_done = (unsigned int *)((char *)W->counters.p + 8);
     CK(prof_mark(W, true, s));
@@ -662,7 +676,9 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     CK(prof_mark(W, false, s));
     if (single) W->la_clean = true;
     if (prec == 1 && guard_tol > 0.0) {
-        // precision guard: recompute flagged items in float-float
+        // precision guard: the items whose estimate exceeds guard_tol are
+        // recomputed in float-float, which flags again those whose float-float
+        // estimate still exceeds it; those are recomputed in FP64
         CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
         sa.tab32 = nullptr;
         sa.tabff = (float4 *)W->tabff.p;
@@ -670,11 +686,23 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
         sa.do_items = 0;
         CK(sg_launch_setup(sa, s));
         fa.tab = W->tabff.p;
+        fa.wtab = P->d_wtff;
         fa.skip_unflagged = (int *)W->flags.p;
-        fa.guard_tol = 0.0;
+        fa.guard_tol = guard_tol;
         fa.unit_roundoff = unit_roundoff(2);
         CK(prof_mark(W, true, s));
         CK(sg_launch_fold(fa, 2, 0, fold_cfg(P, 2, C), s));
+        CK(prof_mark(W, false, s));
+        CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
+        sa.tabff = nullptr;
+        sa.tab64 = (double2 *)W->tab64.p;
+        CK(sg_launch_setup(sa, s));
+        fa.tab = W->tab64.p;
+        fa.wtab = P->d_wt64;
+        fa.guard_tol = 0.0;
+        fa.unit_roundoff = unit_roundoff(0);
+        CK(prof_mark(W, true, s));
+        CK(sg_launch_fold(fa, 0, 0, fold_cfg(P, 0, C), s));
         CK(prof_mark(W, false, s));
     }
     // leave the counters of the single-integral fold as it expects them
@@ -686,29 +714,21 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
 // entry points
 // ---------------------------------------------------------------------------
 
-// The form SG_FORM_AUTO stands for.  For a rule that is not nested
-// (Gauss-Legendre) the difference forms evaluate the union of two node sets
-// per active direction, several times the n_d^q points of Eq. 2.6, while the
-// combination form evaluates exactly n_d^q; its price is the binomial
-// coefficients C(d-1, L-k), which multiply the rounding errors of the
-// subgrid sums.  In FP64, with every coefficient at most 1024 (for example
-// d = 12, L = 6: at most C(11, 5) = 462), the combination form keeps far
-// below 1e-12 and takes it; everywhere else the telescoped form.
-static sg_form auto_form(sg_rule rule, int d, int L, int prec) {
-    if (prec == SG_PREC_FP64 && (rule->kind & ~SG_KIND_SLOW) == SG_RULE_GAUSS_LEGENDRE && L >= 1) {
-        unsigned __int128 cmax = 0;
-        for (int j = 0; j <= L && j <= d - 1; j++) cmax = std::max(cmax, binom128(d - 1, j));
-        if (cmax <= 1024) return SG_FORM_COMBINATION;
-    }
-    return SG_FORM_TELESCOPED;
-}
+// The form SG_FORM_AUTO stands for: the merged form (every distinct point
+// of the sparse grid once, with its merged weight).  It evaluates the fewest
+// points (n_d^q / 7.6 for Clenshaw-Curtis at d = 200, L = 5; fewer than the
+// n_d^q of Eq. 2.6 for Gauss-Legendre, whose difference forms need 2l - 1
+// nodes per active direction), and since merging adds terms that share a
+// point, its sum of |w_p D_p| is no larger than the difference form's: no
+// worse conditioned, and unlike Eq. 2.6 free of binomial coefficients.
+static sg_form auto_form(sg_rule, int, int, int) { return SG_FORM_MERGED; }
 
 static sg_status check_one(sg_rule rule, sg_family fam, int d, int q, sg_precision prec,
                            sg_form *form) {
     if (!rule) return SG_EINVAL;
     if ((int)fam < 0 || (int)fam > 4) return SG_EINVAL;
     if (!prec_ok(prec)) return SG_EINVAL;
-    if ((int)*form < 0 || (int)*form > 3) return SG_EINVAL;
+    if ((int)*form < 0 || (int)*form > 4) return SG_EINVAL;
     if (d < 1 || q < d) return SG_EINVAL;
     if (*form == SG_FORM_AUTO) *form = auto_form(rule, d, q - d, prec);
     if (d > SG_MAX_D) return SG_ERANGE;
@@ -734,7 +754,7 @@ static void fill_result(const SgOutDev &o, const Plan *P, int g, double ms, sg_r
 extern "C" sg_status sg_count_points(sg_rule rule, int d, int q, sg_form form, uint64_t *points,
                                      uint64_t *evals) {
     if (!rule || !points) return SG_EINVAL;
-    if ((int)form < 0 || (int)form > 3) return SG_EINVAL;
+    if ((int)form < 0 || (int)form > 4) return SG_EINVAL;
     if (d < 1 || q < d) return SG_EINVAL;
     if (form == SG_FORM_AUTO) form = auto_form(rule, d, q - d, SG_PREC_FP64);
     if (d > SG_MAX_D) return SG_ERANGE;
@@ -919,7 +939,7 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     ST(get_ws(s, &W));
     const bool guard = prec == SG_PREC_MIXED && guard_tol > 0.0;
-    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, prec == SG_PREC_FF || guard,
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64 || guard, prec == SG_PREC_FF || guard,
                   params_on_device ? 0 : pool));
     ST(ensure_host(W, (size_t)P->nout * sizeof(SgOutDev)));
     // graphs run on the workspace's own stream, ordered after the caller's work

@@ -215,13 +215,19 @@ SG_FX double sg_fx_osc_dev(double H, const SgFxPhase &ph) {
 }
 
 // w sin(H) sin(phi + H) for |H| <= 0.7854: the product H B w formed from B
-// and the normalised significands of H and w, rounded once
-SG_FX double sg_fx_osc_dev_w(double H, double w, const SgFxPhase &ph) {
-    const SgFxNorm h = sg_fx_norm(H), g = sg_fx_norm(w);
+// and the normalised significands of H and w, rounded once; g is w as a
+// normalised 64-bit significand (sg_fx_norm of a double, or a weight kept to
+// 64 bits)
+SG_FX double sg_fx_osc_dev_wn(double H, const SgFxNorm &g, const SgFxPhase &ph) {
+    const SgFxNorm h = sg_fx_norm(H);
     sg_u64 nb;
     const sg_u64 b = sg_fx_osc_b(sg_fx_fix(H, 64), 0ull - h.neg, ph, &nb);
     const sg_u64 v = sg_fx_mulhi(sg_fx_mulhi(b, h.m), g.m);  // |H B w| 2^(2105 - eH - ew)
     return sg_fx_to_double_f(v, (nb ^ h.neg ^ g.neg) & 1ull, 2105 - h.e - g.e);
+}
+
+SG_FX double sg_fx_osc_dev_w(double H, double w, const SgFxPhase &ph) {
+    return sg_fx_osc_dev_wn(H, sg_fx_norm(w), ph);
 }
 
 // P(x) of expm1(x) = x + x^2 P(x) in 0.64, for a = |x| in 0.64, |x| <= ln2/2
@@ -250,12 +256,25 @@ SG_FX double sg_fx_expm1(double x) {
 }
 
 // w expm1(x) for |x| <= ln2/2: the product x (1 + x P(x)) w formed from the
-// normalised significands of x and w, rounded once
-SG_FX double sg_fx_expm1_w(double x, double w) {
-    const SgFxNorm h = sg_fx_norm(x), g = sg_fx_norm(w);
+// normalised significands of x and w, rounded once (g: w as a normalised
+// 64-bit significand)
+SG_FX double sg_fx_expm1_wn(double x, const SgFxNorm &g) {
+    const SgFxNorm h = sg_fx_norm(x);
     const sg_u64 a = sg_fx_fix(x, 64), n = 0ull - h.neg;
     const sg_u64 t = sg_fx_mulhi(a, sg_fx_expm1_p(a, n)) >> 2;  // |x| P(x), 2.62
     const sg_u64 k = (1ull << 62) + ((t ^ n) - n);               // 1 + x P(x), 2.62
     const sg_u64 v = sg_fx_mulhi(sg_fx_mulhi(k, h.m), g.m);       // |x k w| 2^(2106 - ex - ew)
     return sg_fx_to_double_f(v, (h.neg ^ g.neg) & 1ull, 2106 - h.e - g.e);
+}
+
+SG_FX double sg_fx_expm1_w(double x, double w) { return sg_fx_expm1_wn(x, sg_fx_norm(w)); }
+
+// A weight kept to 64 bits (SgFxNorm) split into two doubles hi + lo: hi its
+// leading 53 bits, lo the remaining 11 (both exact; 0 below the normal range)
+SG_FX void sg_fx_norm_split(const SgFxNorm &g, double *hi, double *lo) {
+    const sg_u64 s = g.neg << 63;
+    *hi = g.e >= 1 ? sg_fx_from_bits(s | ((sg_u64)g.e << 52) | ((g.m >> 11) & 0xfffffffffffffull)) : 0.0;
+    const int el = g.e - 63;  // biased exponent of 2^(e - 1086), the unit of m's last bit
+    const sg_u64 low = g.m & 0x7ffull;
+    *lo = (low && el >= 1) ? sg_fx_from_bits(s | ((sg_u64)el << 52)) * (double)low : 0.0;
 }

@@ -36,6 +36,8 @@
 #define SG_BLK_DELTA 0  // J^{k+1} - J^k on the union node set, k >= 1
 #define SG_BLK_FULL 1   // J^{k+1}, k >= 1
 #define SG_BLK_TAIL 2   // J^{M+1} - J^1, M >= 1 (telescoped last direction)
+#define SG_BLK_NEW 3    // the nodes level k+1 adds to levels 1..k, k >= 1 (merged form;
+                        // the point weights come from a per-pattern table)
 
 // One integral (or one adjoint sub-sum) as the kernels see it.
 struct SgItemDev {
@@ -91,6 +93,8 @@ struct SgPatDev {
     int asplit;                // chunks per subset (prefix-tuple blocks); 1 = no split
     int ablk;                  // prefix tuples per block when split
     unsigned long long chunk0; // first global chunk of this pattern
+    long long woff;            // merged form: first weight of the pattern (weights of prefix
+                               // tuple a, tail node j at woff + a * tm + j); -1 otherwise
 };
 
 // Chunks per reduction group: the warp that completes the last chunk of a
@@ -104,10 +108,22 @@ struct alignas(32) SgGroupSlot {
     double s, c, abs, pad;
 };
 
-// Per-chunk partial result (written once by the warp that ran the chunk).
-struct alignas(16) SgSlot {
+// A merged-form point weight for the FP64 fold, kept to 64 significant
+// bits: |w| = m 2^(e - 1086) with m's leading one at bit 63, sign neg.
+struct alignas(16) SgW64 {
+    unsigned long long m;
+    int e;
+    int neg;
+};
+
+// Per-chunk partial result (written once by the warp that ran the chunk):
+// the chunk's sum as sum + lo (lo is the rest of an exact sum that the FP64
+// merged fold keeps below the double sum; 0 elsewhere) and its absolute sum.
+struct alignas(32) SgSlot {
     double sum;
     double abs;
+    double lo;
+    double pad;
 };
 
 // Per-output record on the device (matches sg_dev_result's first fields).
@@ -158,7 +174,7 @@ struct SgFoldArgs {
     int *flags;                      // guard flags per item (written when guard_tol > 0)
     const int *skip_unflagged;       // if non-NULL: only items with flags[item] != 0 are run
     double guard_tol;
-    double unit_roundoff;            // 2^-24 or 2^-53
+    double unit_roundoff;            // effective unit roundoff: err_est = 0.05 * this * cond
     // Single-integral plans (one forward item, no guard): every chunk's sum
     // goes into a long accumulator in the CTA's shared memory (sg_lacc.h),
     // each CTA adds its accumulator into the launch's accumulator `lacc`
@@ -170,4 +186,7 @@ struct SgFoldArgs {
     int single;
     long long *lacc;
     unsigned int *cta_done;
+    // merged form: point weights of every pattern (SgW64 for the FP64 fold,
+    // float pairs hi + lo for the float and float-float folds)
+    const void *wtab;
 };

@@ -229,6 +229,35 @@ __device__ __forceinline__ double gdevw_d(double S, double w, double sphi, doubl
     }
 }
 
+// The same with the weight kept to 64 bits (merged form): the fixed-point
+// product takes the whole significand; the paths through the double
+// functions add the weight's low part with one more multiply-add.
+template <int GK>
+__device__ __forceinline__ double gdevw_dn(double S, const SgFxNorm &g, double sphi, double cphi,
+                                           const SgFxPhase &ph) {
+    const int hx = __double2hiint(S) & 0x7fffffff;
+    if constexpr (GK == SG_GK_EXPM1) {
+        double v = sg_fx_expm1_wn(S, g);
+        if (hx >= 0x3fd62e42) {
+            double whi, wlo;
+            sg_fx_norm_split(g, &whi, &wlo);
+            const double e = sg_expm1_d(S);
+            v = fma(e, whi, e * wlo);
+        }
+        return v;
+    } else {
+        double v = sg_fx_osc_dev_wn(S, g, ph);
+        if (hx >= 0x3fe921fb) {
+            double sh, ch, whi, wlo;
+            sg_sincos_d(S, &sh, &ch);
+            sg_fx_norm_split(g, &whi, &wlo);
+            const double t = sh * fma(sphi, ch, cphi * sh);
+            v = fma(t, whi, t * wlo);
+        }
+        return v;
+    }
+}
+
 // Float-float deviation (see sg_ff.cuh): expm1, or for the oscillatory kind
 // sin(H) sin(phi + H) = sin(H) (sin(phi) cos(H) + cos(phi) sin(H)).
 template <int GK> __device__ __forceinline__ ff2 gdev_ff(ff2 S, ff2 sphi, ff2 cphi) {
@@ -263,6 +292,13 @@ struct FoldAcc {
     double acc = 0.0;
     float hs = 0.f, hc = 0.f, habs = 0.f;
     ff2 fa = {0.f, 0.f};  // float-float path
+    // FP64 merged path: an exact running sum in a 128-bit window whose unit
+    // follows the largest term (sg_xsum.h).  The merged weights are large
+    // and of both signs, and rounding a double running sum after each of
+    // their terms costs digits the difference forms, with many more and
+    // smaller terms, do not lose.
+    SgX xa = {0ull, 0ull};
+    int xe = 1;
 };
 
 // Prefix state of one prefix node tuple: partial argument S and weight W.
@@ -278,14 +314,25 @@ __device__ __forceinline__ V2 tail_entry(const V2 *__restrict__ tab, long long b
     return tab[e < E1 ? base1 + e : base2 + (e - E1)];
 }
 
+// Weights of a merged-form pattern (SgFoldArgs::wtab + SgPatDev::woff): the
+// point of prefix tuple a and tail node j has weight wt[a * tm + j].
+struct SgMergedW {
+    const void *wt;
+    int tm;
+    SgDivMagic dm;  // division by tm
+};
+
 // Folds the points (prefix tuple a < At) x (tail entries e < E1 + E2) of one
 // run.  Tail entries come from up to two contiguous table segments (two
-// when the enumerated directions jump over a left-out direction).
-template <typename T, int GK>
+// when the enumerated directions jump over a left-out direction).  With MW
+// (merged form) the weight of a point is read from the pattern's weight
+// table (prefix tuple ab + a, tail node e mod tm) instead of being the
+// product of the prefix and tail weights.
+template <typename T, int GK, bool MW>
 __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict__ tab,
                                          long long base1, int E1, long long base2, int E2,
                                          const typename PrefixState<T>::type *sP, int At, T sphi,
-                                         T cphi, int lane, FoldAcc &F) {
+                                         T cphi, int lane, FoldAcc &F, const SgMergedW &M, int ab) {
     typedef typename V2T<T>::type V2;
     const int E = E1 + E2;
     if constexpr (sizeof(T) == 4) {
@@ -299,16 +346,27 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
         float hs = F.hs, hc = F.hc, habs = F.habs;
         for (int e = g.e0; e < E; e += g.estep) {
             const V2 te = tab[e < E1 ? base1 + e : base2 + (e - E1)];
+            // merged weights as float pairs: one weight serves every subset of
+            // its pattern, so its rounding error would add up coherently; the
+            // low part costs one more FMA per point
+            const float2 *wrow = nullptr;
+            if constexpr (MW) wrow = (const float2 *)M.wt + (e - sg_div_magic_q(e, M.dm) * M.tm) + (size_t)ab * M.tm;
             int a = g.a0;
             for (; a + 7 * g.astep < At; a += 8 * g.astep) {
                 float part = 0.f;
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const float2 p = sP[a + u * g.astep];
-                    const float W = p.y * te.y;
                     const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
-                    part = fmaf(W, D, part);
-                    habs = fmaf(fabsf(W), fabsf(D), habs);
+                    if constexpr (MW) {
+                        const float2 w = __ldg(wrow + (size_t)(a + u * g.astep) * M.tm);
+                        part = fmaf(w.x, D, fmaf(w.y, D, part));
+                        habs = fmaf(fabsf(w.x), fabsf(D), habs);
+                    } else {
+                        const float W = p.y * te.y;
+                        part = fmaf(W, D, part);
+                        habs = fmaf(fabsf(W), fabsf(D), habs);
+                    }
                 }
                 float t, err;
                 two_sum(hs, part, t, err);
@@ -318,10 +376,16 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
             float part = 0.f;
             for (; a < At; a += g.astep) {
                 const float2 p = sP[a];
-                const float W = p.y * te.y;
                 const float D = gdev<float, GK>(p.x + te.x, sphi, cphi);
-                part = fmaf(W, D, part);
-                habs = fmaf(fabsf(W), fabsf(D), habs);
+                if constexpr (MW) {
+                    const float2 w = __ldg(wrow + (size_t)a * M.tm);
+                    part = fmaf(w.x, D, fmaf(w.y, D, part));
+                    habs = fmaf(fabsf(w.x), fabsf(D), habs);
+                } else {
+                    const float W = p.y * te.y;
+                    part = fmaf(W, D, part);
+                    habs = fmaf(fabsf(W), fabsf(D), habs);
+                }
             }
             float t, err;
             two_sum(hs, part, t, err);
@@ -340,17 +404,29 @@ __device__ __forceinline__ void fold_run(const typename V2T<T>::type *__restrict
         for (; f.a < At; f.step()) {
             const double2 p = sP[f.a];
             const V2 te = tail_entry(tab, base1, E1, base2, f.e);
-            acc = fma(p.y, gdevw_d<GK>(p.x + te.x, te.y, sphi, cphi, ph), acc);
+            if constexpr (MW) {
+                // the weight to 64 bits: it serves every subset of its pattern,
+                // so its rounding error would add up coherently over them
+                const int j = f.e - sg_div_magic_q(f.e, M.dm) * M.tm;
+                const ulonglong2 w = __ldg((const ulonglong2 *)M.wt + (size_t)(ab + f.a) * M.tm + j);
+                SgFxNorm g;  // SgW64: m, then e and neg in the second word
+                g.m = w.x;
+                g.e = (int)(unsigned)w.y;
+                g.neg = w.y >> 32;
+                sg_x_add_adaptive(F.xa, F.xe, gdevw_dn<GK>(p.x + te.x, g, sphi, cphi, ph));
+            } else {
+                acc = fma(p.y, gdevw_d<GK>(p.x + te.x, te.y, sphi, cphi, ph), acc);
+            }
         }
         F.acc = acc;
     }
 }
 
 // Float-float fold of one run (same lane layout as fold_run).
-template <int GK>
+template <int GK, bool MW>
 __device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long long base1, int E1,
                                             long long base2, int E2, const float4 *sP, int At, ff2 sphi,
-                                            ff2 cphi, int lane, FoldAcc &F) {
+                                            ff2 cphi, int lane, FoldAcc &F, const SgMergedW &M, int ab) {
     SgFlatPos f(lane, E1 + E2);
     ff2 fa = F.fa;
     float habs = F.habs;
@@ -358,7 +434,14 @@ __device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long
         const float4 p = sP[f.a];
         const float4 te = tail_entry(tab, base1, E1, base2, f.e);
         const ff2 S = ff_add(ff2{p.x, p.y}, ff2{te.x, te.y});
-        const ff2 W = ff_mul(ff2{p.z, p.w}, ff2{te.z, te.w});
+        ff2 W;
+        if constexpr (MW) {
+            const int j = f.e - sg_div_magic_q(f.e, M.dm) * M.tm;
+            const float2 w = __ldg((const float2 *)M.wt + (size_t)(ab + f.a) * M.tm + j);
+            W = ff2{w.x, w.y};
+        } else {
+            W = ff_mul(ff2{p.z, p.w}, ff2{te.z, te.w});
+        }
         const ff2 D = gdev_ff<GK>(S, sphi, cphi);
         fa = ff_add(fa, ff_mul(W, D));
         habs = fmaf(fabsf(W.hi), fabsf(D.hi), habs);
@@ -367,7 +450,7 @@ __device__ __forceinline__ void fold_run_ff(const float4 *__restrict__ tab, long
     F.habs = habs;
 }
 
-template <typename T, int GK>
+template <typename T, int GK, bool MW>
 __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                            const SgItemDev *__restrict__ I, unsigned long long c,
                            typename PrefixState<T>::type *sP, SgPrefixPos *sPos, int *sIdx, int lane,
@@ -403,6 +486,13 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
     typedef typename std::conditional<std::is_same<T, FFTag>::value, float, T>::type TS;
     const TS sphi = (TS)V->sin_phi, cphi = (TS)V->cos_phi;
     const ff2 ffsphi = ff_from_double(V->sin_phi), ffcphi = ff_from_double(V->cos_phi);
+    SgMergedW M;
+    if constexpr (MW) {
+        M.tm = tm;
+        M.dm = sg_div_magic(tm);
+        M.wt = sizeof(T) == 8 ? (const void *)((const SgW64 *)A.wtab + P->woff)
+                              : (const void *)((const float2 *)A.wtab + P->woff);
+    }
     while (cnt > 0) {
         const int plast = sIdx[r - 1];
         const int run = (unsigned long long)(d - plast) < cnt ? d - plast : (int)cnt;
@@ -424,7 +514,7 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                         const V2 e = tab[pp.row + (q - qn * pp.m)];
                         q = qn;
                         S = ff_add(S, ff2{e.x, e.y});
-                        W = ff_mul(W, ff2{e.z, e.w});
+                        if constexpr (!MW) W = ff_mul(W, ff2{e.z, e.w});
                     }
                     sP[a] = make_float4(S.hi, S.lo, W.hi, W.lo);
                 } else {
@@ -435,7 +525,7 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
                         const V2 e = tab[pp.row + (q - qn * pp.m)];
                         q = qn;
                         S += e.x;
-                        W *= e.y;
+                        if constexpr (!MW) W *= e.y;
                     }
                     sP[a].x = S;
                     sP[a].y = W;
@@ -443,9 +533,11 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
             }
             __syncwarp();
             if constexpr (std::is_same<T, FFTag>::value)
-                fold_run_ff<GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, ffsphi, ffcphi, lane, F);
+                fold_run_ff<GK, MW>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, ffsphi, ffcphi, lane, F,
+                                    M, ab);
             else
-                fold_run<T, GK>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, sphi, cphi, lane, F);
+                fold_run<T, GK, MW>(tab, seg.base1, seg.E1, seg.base2, seg.E2, sP, At, sphi, cphi, lane, F, M,
+                                    ab);
             __syncwarp();
         }
         cnt -= run;
@@ -553,13 +645,26 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         if (A.skip_unflagged && !A.flags[item]) continue;
         const SgItemDev *I = A.items + item;
         FoldAcc F;
-        if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
-        else fold_chunk<T, SG_GK_EXPM1>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+        if (P->woff >= 0 && A.wtab) {
+            if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC, true>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+            else fold_chunk<T, SG_GK_EXPM1, true>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+        } else {
+            if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC, false>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+            else fold_chunk<T, SG_GK_EXPM1, false>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
+        }
         // the chunk's sum over the lanes, exact before one rounding
-        double acc, aabs;
+        double acc, aabs, acc_lo = 0.0;
         if constexpr (std::is_same<T, double>::value) {
             // the FP64 fold skips |W D| per point: the chunk's |sum| stands in
-            acc = warp_sum(F.acc);
+            if (P->woff >= 0 && A.wtab) {
+                // merged: the lanes' exact sums, aligned and added exactly, kept as
+                // a pair of doubles
+                const int E = warp_max_exp(F.xe);
+                sg_x_shr(F.xa, E - F.xe);
+                warp_xsum(F.xa, E, acc, acc_lo);
+            } else {
+                acc = warp_sum(F.acc);
+            }
             aabs = fabs(acc);
         } else {
             acc = warp_sum(std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa));
@@ -568,11 +673,12 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         const double cf = P->coef;  // 1 for most patterns: skip two dependent FP64 steps
         const double vsum = cf == 1.0 ? acc : acc * cf, vabs = cf == 1.0 ? aabs : aabs * fabs(cf);
         if (A.single) {
-            // lane k adds digit k of the chunk's sum and absolute sum into the
-            // CTA's long accumulator (at most three lanes of each are non-zero,
-            // and no two lanes share a limb)
+            // lane k adds digit k of the chunk's sum (both parts) and absolute
+            // sum into the CTA's long accumulator (at most three lanes of each
+            // are non-zero, and no two lanes share a limb)
             int ovf = 0;
-            const long long d1 = sg_la_digit(vsum, lane, &ovf), d2 = sg_la_digit(vabs, lane, &ovf);
+            const long long d1 = sg_la_digit(vsum, lane, &ovf) + sg_la_digit(acc_lo, lane, &ovf);
+            const long long d2 = sg_la_digit(vabs, lane, &ovf);
             if (d1) atomicAdd((unsigned long long *)&s_la[lane], (unsigned long long)d1);
             if (d2) atomicAdd((unsigned long long *)&s_la[SG_LA_DIGITS + lane], (unsigned long long)d2);
             if (ovf) s_flag[0] = 1;
@@ -582,6 +688,8 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
             SgSlot sl;
             sl.sum = vsum;
             sl.abs = vabs;
+            sl.lo = acc_lo;
+            sl.pad = 0.0;
             A.slots[c] = sl;
         }
         complete_chunk(A, item, c, lane);

@@ -10,7 +10,7 @@
 // All device scratch of this entry point (the per-direction tables, the
 // per-chunk and per-group slots, tickets, the plan and rule nodes, and the
 // binomial table used for unranking) lives in one file-scope
-// `static __device__` array of fixed size (kNaBytes, about 4.2 MB), which
+// `static __device__` array of fixed size (kNaBytes, about 5.2 MB), which
 // every GPU that loads this library holds until the process exits.  Host
 // planning uses only the stack; the 1-D rules are computed into stack
 // arrays.  The kernels are the library's regular setup / prep / fold
@@ -269,6 +269,7 @@ sg_status na_plan(int kind, int fam, int d, int L, int prec, long long resident_
         if (nsub == 0) continue;
         SgPatDev &pd = P.pats[P.npat];
         memset(&pd, 0, sizeof(pd));
+        pd.woff = -1;  // weights are products of the block weights (not the merged form)
         pd.item = 0;
         pd.r = spec[i].r;
         unsigned long long A = 1;
@@ -303,6 +304,7 @@ sg_status na_plan(int kind, int fam, int d, int L, int prec, long long resident_
     P.nchunks = chunk;
     if (P.npat == 0) {
         memset(&P.pats[0], 0, sizeof(SgPatDev));
+        P.pats[0].woff = -1;
         P.pat_chunk0[0] = ~0ull;
     }
     memset(&P.item, 0, sizeof(P.item));
@@ -404,7 +406,7 @@ extern "C" sg_status sg_integrate_noalloc(sg_rule_kind kind, sg_family fam, cons
     sa.bases = (SgBaseDev *)(S + kOffBase);
     sa.flags = nullptr;
     NA_CK(sg_launch_setup(sa, s));
-    const double u = p ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    const double u = p ? 5.9604644775390625e-07 : 1.1102230246251565e-16;  // as the other entry points
     SgPrepArgs pa;
     pa.roles = (const SgItemRole *)(S + kOffRole);
     pa.items = (const SgItemDev *)(S + kOffItem);

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 
 unsigned __int128 binom128(long long n, int k) {
@@ -64,6 +65,21 @@ void gen_patterns(int form, int d, int L, std::vector<PatSpec> &out) {
         }
         return;
     }
+    if (form == SG_FORM_MERGED) {
+        // every distinct point: compositions (e_1..e_r) of K <= L into the
+        // excesses at which the point's active coordinates first appear;
+        // blocks NEW(e), weights from merged_weights
+        for (int K = 1; K <= L; K++)
+            for (int r = 1; r <= std::min(K, d); r++) {
+                std::vector<std::vector<int>> comps;
+                compositions(K, r, cur, comps);
+                for (auto &c : comps) {
+                    std::vector<int> pre(c.begin(), c.end() - 1);
+                    add(pre, SG_BLK_NEW, BlockRef{SG_BLK_NEW, c.back()}, 1.0);
+                }
+            }
+        return;
+    }
     int Klo = 1;
     if (form == SG_FORM_COMBINATION) Klo = std::max(1, L - d + 1);
     for (int K = Klo; K <= L; K++) {
@@ -99,6 +115,164 @@ void drop_empty_patterns(sg_rule rule, std::vector<PatSpec> &specs) {
                                    return false;
                                }),
                 specs.end());
+}
+
+// ---- merged-form weights ----------------------------------------------------
+//
+// A point of the sparse grid has, in each direction i, a node nu_i that
+// first appears at level h_i = e_i + 1 (the centre at level 1: e_i = 0).
+// Collecting the difference-form terms (Eq. 2.9 read as tensor products of
+// difference rules) of every subgrid k that contains it, its weight is
+//   w = sum_{k >= e, |k| <= L} prod_i (w^{k_i + 1}(nu_i) - w^{k_i}(nu_i))
+//     = sum_{t <= L} [z^t] prod_{i active} A_{nu_i}(z) * B(z)^(d - r),
+// with A_nu(z) = sum_{k >= e} (w^{k+1}(nu) - w^k(nu)) z^k and B the same
+// series of the centre (w^l(x): the level-l weight at node x, 0 where x is
+// not a node of level l).  The weight depends on the active directions'
+// nodes only, not on which directions they are, so one table per pattern
+// (e_1..e_r) serves all C(d, r) subsets.  Everything is formed in
+// double-double arithmetic (Dekker 1971) and rounded once per format.
+
+namespace {
+
+struct DD {
+    double hi, lo;
+};
+
+DD dd_two_sum(double a, double b) {
+    const double s = a + b, z = s - a;
+    return DD{s, (a - (s - z)) + (b - z)};
+}
+
+DD dd_add(DD a, DD b) {
+    DD s = dd_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return dd_two_sum(s.hi, s.lo);
+}
+
+DD dd_mul(DD a, DD b) {
+    const double p = a.hi * b.hi;
+    const double e = std::fma(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+    return dd_two_sum(p, e);
+}
+
+typedef std::vector<DD> Poly;  // coefficients of z^0 .. z^L
+
+Poly poly_mul(const Poly &a, const Poly &b, int L) {
+    Poly c(L + 1, DD{0.0, 0.0});
+    for (int i = 0; i <= L; i++) {
+        if (a[i].hi == 0.0 && a[i].lo == 0.0) continue;
+        for (int j = 0; i + j <= L; j++) c[i + j] = dd_add(c[i + j], dd_mul(a[i], b[j]));
+    }
+    return c;
+}
+
+// hi + lo as a 64-bit significand and exponent (SgW64): hi's 53 bits, then
+// lo in units of 2^-11 of hi's last place, rounded to nearest
+SgW64 w64(DD w) {
+    SgW64 r;
+    r.m = 0;
+    r.e = 1;
+    r.neg = 0;
+    if (w.hi == 0.0) return r;
+    unsigned long long b;
+    memcpy(&b, &w.hi, sizeof(b));
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return r;  // below the normal range: no merged weight is that small
+    r.neg = (int)(b >> 63);
+    unsigned long long m = ((b & 0xfffffffffffffull) | (1ull << 52)) << 11;
+    const double lu = std::ldexp(r.neg ? -w.lo : w.lo, 1086 - e);  // |lu| <= 2^10
+    m += (unsigned long long)(long long)std::llround(lu);
+    if (!(m >> 63)) {
+        m <<= 1;
+        e -= 1;
+    }
+    r.m = m;
+    r.e = e;
+    return r;
+}
+
+// weight of node x in level l (0 for l = 0 or where x is not a node)
+double level_weight(const std::vector<std::vector<double>> &lx, const std::vector<std::vector<double>> &lw,
+                    int l, double x) {
+    if (l < 1) return 0.0;
+    const auto &X = lx[l];
+    auto it = std::lower_bound(X.begin(), X.end(), x);
+    return (it != X.end() && *it == x) ? lw[l][it - X.begin()] : 0.0;
+}
+
+}  // namespace
+
+bool merged_weights(sg_rule rule, int d, int L, double factor, std::vector<PatSpec> &specs, Plan *P) {
+    std::vector<std::vector<double>> lx(L + 2), lw(L + 2);
+    for (int l = 1; l <= L + 1; l++) {
+        const int n = sg_level_nodes(rule->kind, l);
+        lx[l].resize(n);
+        lw[l].resize(n);
+        sg_rule_level(rule->kind, l, lx[l].data(), lw[l].data());
+    }
+    auto series = [&](double x, int e) {
+        Poly a(L + 1, DD{0.0, 0.0});
+        for (int k = e; k <= L; k++)
+            a[k] = dd_two_sum(level_weight(lx, lw, k + 1, x), -level_weight(lx, lw, k, x));
+        return a;
+    };
+    // B(z)^n for the n = d - r a pattern needs, cumulated: Bc_n[m] = sum_{j<=m} [z^j] B^n
+    const Poly B = series(0.5, 0);
+    std::map<int, Poly> bcum;
+    for (auto &sp : specs) {
+        const int n = d - sp.r;
+        if (bcum.count(n)) continue;
+        Poly acc(L + 1, DD{0.0, 0.0}), base = B;
+        acc[0] = DD{1.0, 0.0};
+        for (int e = n; e > 0; e >>= 1) {
+            if (e & 1) acc = poly_mul(acc, base, L);
+            if (e > 1) base = poly_mul(base, base, L);
+        }
+        for (int m = 1; m <= L; m++) acc[m] = dd_add(acc[m], acc[m - 1]);
+        bcum[n] = acc;
+    }
+    // the nodes each excess adds, with their series
+    std::vector<std::vector<Poly>> A(L + 1);
+    for (int e = 1; e <= L; e++)
+        for (double x : rule->x[SG_BLK_NEW][e]) A[e].push_back(series(x, e));
+    for (auto &sp : specs) {
+        int ex[SG_MAX_R];
+        for (int t = 0; t < sp.r - 1; t++) ex[t] = sp.pre[t].k;
+        ex[sp.r - 1] = sp.tail.k;
+        int K = 0;
+        size_t cnt = 1;
+        for (int t = 0; t < sp.r; t++) {
+            K += ex[t];
+            cnt *= A[ex[t]].size();
+        }
+        if (P->wt64.size() + cnt > ((size_t)1 << 24)) return false;
+        sp.woff = (long long)P->wt64.size();
+        const Poly &bc = bcum[d - sp.r];
+        // depth-first over the node tuple, the last position fastest, with the
+        // partial products kept per depth
+        std::vector<Poly> part(sp.r + 1);
+        part[0] = Poly(L + 1, DD{0.0, 0.0});
+        part[0][0] = DD{1.0, 0.0};
+        std::vector<int> idx(sp.r, 0);
+        int t = 0;
+        for (;;) {
+            if (t == sp.r) {
+                DD w = {0.0, 0.0};
+                for (int s = K; s <= L; s++) w = dd_add(w, dd_mul(part[sp.r][s], bc[L - s]));
+                w.hi *= factor;
+                w.lo *= factor;
+                P->wt64.push_back(w64(w));
+                const float hf = (float)w.hi;
+                P->wtff.push_back(make_float2(hf, (float)((w.hi - (double)hf) + w.lo)));
+                t--;
+                while (t >= 0 && ++idx[t] == (int)A[ex[t]].size()) idx[t--] = 0;
+                if (t < 0) break;
+            }
+            part[t + 1] = poly_mul(part[t], A[ex[t]][idx[t]], L);
+            t++;
+        }
+    }
+    return true;
 }
 
 // n_d^q of Eq. 2.6: sum over the combination-form multi-indices of
@@ -176,9 +350,19 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
             b.form = R.form;
             gen_patterns(R.form, d_item, L_item, b.specs);
             drop_empty_patterns(rule, b.specs);
+            // merged form: the point weights (with the factor -2 of the
+            // oscillatory deviation, which the other forms fold into the
+            // prefix weight)
+            if (R.form == SG_FORM_MERGED &&
+                !merged_weights(rule, d_item, L_item, gk == SG_GK_OSC ? -2.0 : 1.0, b.specs, P))
+                return false;
             ib.push_back(b);
+            return true;
         };
-        new_item(SG_ROLE_FORWARD, -1, 0.0, R.d, -1, R.L, g);
+        if (!new_item(SG_ROLE_FORWARD, -1, 0.0, R.d, -1, R.L, g)) {
+            plan_free_host(P);
+            return SG_ERANGE;
+        }
         if (R.grad) {
             if (R.fam == SG_FAM_OSCILLATORY)
                 new_item(SG_ROLE_FORWARD_SHIFT, -1, 0.0, R.d, -1, R.L, shift_out++);
@@ -314,6 +498,7 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
             pd.tm = tab_m(rule, sp.tail);
             pd.toff = relmap[g].at(sp.tail);
             pd.coef = sp.coef;
+            pd.woff = sp.woff;
             const u64 per_sub = A * (u64)pd.tm;
             const u64 nsub = pd.nsub;
             // one record for subsets [r0, r1) with chunk target tgt
@@ -378,6 +563,7 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     if (P->pats.empty()) {  // keep the device arrays non-empty
         SgPatDev pd;
         memset(&pd, 0, sizeof(pd));
+        pd.woff = -1;
         P->pats.push_back(pd);
         P->pat_chunk0.push_back(~0ull);
     }

@@ -13,8 +13,8 @@ typedef unsigned long long u64;
 struct sg_rule_s {
     int kind = 0, max_level = 0, device = 0;
     // blocks [bk][k], k = 1..max_level-1
-    std::vector<double> x[3][SG_MAX_LEVEL], w[3][SG_MAX_LEVEL];
-    int off[3][SG_MAX_LEVEL] = {};
+    std::vector<double> x[4][SG_MAX_LEVEL], w[4][SG_MAX_LEVEL];
+    int off[4][SG_MAX_LEVEL] = {};
     double2 *d_xw = nullptr;  // device copy of all blocks (set by sg_rule_init)
 };
 
@@ -30,6 +30,7 @@ struct PatSpec {
     BlockRef pre[SG_MAX_R - 1];
     BlockRef tail;
     double coef;
+    long long woff = -1;  // merged form: first weight in the plan's weight arrays
 };
 
 struct Req {
@@ -65,6 +66,10 @@ struct Plan {
     int nout = 0;
     long long nv = 0;
     std::vector<u64> points, evals;  // per integral (forward sum only)
+    // merged-form point weights of every pattern that uses them, in the two
+    // formats the folds read (64-bit significands; float pairs hi + lo)
+    std::vector<SgW64> wt64;
+    std::vector<float2> wtff;
     u64 total_evals = 0;             // every item, adjoint included
     int max_d = 0;
     // gradient (single integral)
@@ -82,6 +87,8 @@ struct Plan {
     SgPatDev *d_pats = nullptr;
     u64 *d_pat_chunk0 = nullptr;
     SgChunkStart *d_chunk_start = nullptr;  // per chunk, filled on the device at upload
+    const SgW64 *d_wt64 = nullptr;
+    const float2 *d_wtff = nullptr;
     int *d_delta_off = nullptr, *d_delta_m = nullptr;
     double2 *d_delta_xw = nullptr;  // the rule's block array (borrowed)
     int launch_ctas = 0;
@@ -94,6 +101,10 @@ void gen_patterns(int form, int d, int L, std::vector<PatSpec> &out);
 // Nodes per direction of a rule block.
 int tab_m(sg_rule rule, BlockRef b);
 void drop_empty_patterns(sg_rule rule, std::vector<PatSpec> &specs);
+// Merged-form point weights of the patterns `specs` (d directions, excess
+// budget L) appended to the plan's weight arrays, times `factor`; sets each
+// pattern's woff.  False when there would be more than 2^24 weights.
+bool merged_weights(sg_rule rule, int d, int L, double factor, std::vector<PatSpec> &specs, Plan *P);
 // n_d^q of Eq. 2.6 (false if beyond 64 bits).
 bool count_points(int kind, int d, int L, u64 *out);
 // Builds the host arrays of a plan; device fields stay empty.

@@ -77,19 +77,24 @@ __device__ __forceinline__ double warp_sum(double v) {
     return s;
 }
 
-// Sum of a group's chunk slots (sum, abs): at most SG_GROUP = 64 slots, two
-// per lane, held in registers while the largest exponents are found.
-__device__ inline void reduce_slots(const double2 *slots, unsigned long long n, int lane, double &S,
+// Sum of a group's chunk slots (sum + lo, abs): at most SG_GROUP = 64
+// slots, two per lane, held in registers while the largest exponents are
+// found.
+__device__ inline void reduce_slots(const SgSlot *slots, unsigned long long n, int lane, double &S,
                              double &C, double &AB) {
     static_assert(SG_GROUP <= 64, "two slots per lane");
     const double2 z = make_double2(0.0, 0.0);
-    const double2 v0 = (unsigned long long)lane < n ? __ldcg(slots + lane) : z;
-    const double2 v1 = (unsigned long long)lane + 32 < n ? __ldcg(slots + lane + 32) : z;
-    const int Es = warp_max_exp(max(sg_x_exp(v0.x), sg_x_exp(v1.x)));
+    const double2 v0 = (unsigned long long)lane < n ? __ldcg((const double2 *)(slots + lane)) : z;
+    const double2 v1 = (unsigned long long)lane + 32 < n ? __ldcg((const double2 *)(slots + lane + 32)) : z;
+    const double l0 = (unsigned long long)lane < n ? __ldcg(&slots[lane].lo) : 0.0;
+    const double l1 = (unsigned long long)lane + 32 < n ? __ldcg(&slots[lane + 32].lo) : 0.0;
+    const int Es = warp_max_exp(max(max(sg_x_exp(v0.x), sg_x_exp(v1.x)), max(sg_x_exp(l0), sg_x_exp(l1))));
     const int Ea = warp_max_exp(max(sg_x_exp(v0.y), sg_x_exp(v1.y)));
     SgX as = {0ull, 0ull}, aa = {0ull, 0ull};
     sg_x_add(as, v0.x, Es);
     sg_x_add(as, v1.x, Es);
+    sg_x_add(as, l0, Es);
+    sg_x_add(as, l1, Es);
     sg_x_add(aa, v0.y, Ea);
     sg_x_add(aa, v1.y, Ea);
     double ac;
@@ -153,7 +158,7 @@ __device__ inline void complete_chunk(const SgFoldArgs &A, int item, unsigned lo
     if (ticket + 1ull != gsize) return;
     __syncwarp();
     double S, C, AB;
-    reduce_slots((const double2 *)(A.slots + I->chunk0 + gfirst), gsize, lane, S, C, AB);
+    reduce_slots(A.slots + I->chunk0 + gfirst, gsize, lane, S, C, AB);
     if (lane == 0) {
         SgGroupSlot gs;
         gs.s = S;

@@ -411,6 +411,27 @@ int sg_block(int kind, int bk, int k, double *x, double *w) {
         w[n] = -1.0;
         return n + 1;
     }
+    if (bk == SG_BLK_NEW) {
+        // the nodes of level k+1 that no level <= k has (nested rules repeat
+        // their coarser nodes bit for bit; Gauss-Legendre levels share only
+        // the centre); the weights of a merged-form point come from a
+        // per-pattern table, so the block carries weight 1
+        if (sg_level_member(kind, k + 1) == sg_level_member(kind, k)) return 0;
+        std::vector<double> old;
+        for (int l = 1; l <= k; l++) {
+            const int m = sg_rule_level(kind, l, xb, wb);
+            old.insert(old.end(), xb, xb + m);
+        }
+        std::sort(old.begin(), old.end());
+        int c = 0;
+        for (int j = 0; j < n; j++)
+            if (!std::binary_search(old.begin(), old.end(), xa[j])) {
+                x[c] = xa[j];
+                w[c] = 1.0;
+                c++;
+            }
+        return c;
+    }
     // difference rule; zero (empty block) when both levels use the same member
     if (sg_level_member(kind, k + 1) == sg_level_member(kind, k)) return 0;
     int n0 = sg_rule_level(kind, k, xb, wb);
@@ -438,6 +459,10 @@ int sg_block(int kind, int bk, int k, double *x, double *w) {
 int sg_block_size(int kind, int bk, int k) {
     int n = sg_level_nodes(kind, k + 1);
     if (n == 0 || k < 1) return 0;
+    if (bk == SG_BLK_NEW) {
+        static thread_local double x[2 * 4097 + 2], w[2 * 4097 + 2];
+        return sg_block(kind, bk, k, x, w);
+    }
     if (bk == SG_BLK_FULL) return n;
     if (bk == SG_BLK_TAIL) return (n % 2) ? n : n + 1;
     if (sg_level_member(kind, k + 1) == sg_level_member(kind, k)) return 0;

@@ -21,7 +21,8 @@ int sg_level_nodes(int kind, int level);
 // Level-`level` rule on [0,1], nodes ascending.  Returns the node count.
 int sg_rule_level(int kind, int level, double *x, double *w);
 
-// Block of kind `bk` (SG_BLK_*) at excess k >= 1: nodes/weights on [0,1].
+// Block of kind `bk` (SG_BLK_*) at excess k >= 1: nodes/weights on [0,1]
+// (SG_BLK_NEW: the nodes level k+1 adds, weight 1).
 // x, w need room for 2 * 4097 entries.  Returns the node count (0 if invalid,
 // and for a difference block whose two levels use the same member).
 int sg_block(int kind, int bk, int k, double *x, double *w);

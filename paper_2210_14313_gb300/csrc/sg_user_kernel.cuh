@@ -158,6 +158,8 @@ extern "C" __global__ void sg_user_fold(SgFoldArgs A, SgUserArgs U) {
             SgSlot sl;
             sl.sum = acc * P->coef;
             sl.abs = fabs(acc * P->coef);
+            sl.lo = 0.0;
+            sl.pad = 0.0;
             A.slots[c] = sl;
         }
         complete_chunk(A, item, c, lane, [&](double T, double AB) {

@@ -147,3 +147,19 @@ def lacc(v, nparts=1):
     if out[3]:
         raise AssertionError("%d non-zero digits outside the three added per term" % out[3])
     return out[0], out[1], int(out[2])
+
+
+def merged_points(kind, d, L):
+    """Every point of the merged form (distinct points of the sparse grid
+    except the centre) with the planner's merged weight: (X[n, d], W[n])."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_merged_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_longlong]
+    lib.chk_merged_points.restype = ctypes.c_longlong
+    n = lib.chk_merged_points(kind, d, L, None, None, 0)
+    if n < 0:
+        raise RuntimeError("merged weights failed")
+    X = np.zeros((n, d))
+    W = np.zeros(n)
+    lib.chk_merged_points(kind, d, L, X.ctypes.data_as(dp), W.ctypes.data_as(dp), n)
+    return X, W

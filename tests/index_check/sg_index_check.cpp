@@ -49,6 +49,12 @@ double phi_c(int fam, double a, double u) {
     return 0;
 }
 
+// a merged weight kept to 64 bits, rounded to a double
+double w64_value(const SgW64 &w) {
+    const double v = ldexp((double)w.m, w.e - 1086);
+    return w.neg ? -v : v;
+}
+
 void neu(double &s, double &c, double v) {
     double t = s + v;
     if (fabs(s) >= fabs(v)) c += (s - t) + v;
@@ -74,7 +80,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
     rule.max_level = L + 2 > SG_MAX_LEVEL ? SG_MAX_LEVEL : L + 2;
     std::vector<double> tx(2 * 4097 + 2), tw(2 * 4097 + 2);
     int off = 0;
-    for (int bk = 0; bk < 3; bk++)
+    for (int bk = 0; bk < 4; bk++)
         for (int k = 1; k < rule.max_level; k++) {
             int n = sg_block(kind, bk, k, tx.data(), tw.data());
             rule.x[bk][k].assign(tx.begin(), tx.begin() + n);
@@ -241,9 +247,15 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
                         if (!check(rel, Pp->toff, Pp->tm)) continue;
                         const double2 te = tab[tbase + rel];
                         seen[(size_t)a * E + e]++;
-                        const double Sv = S[ab + a] + te.x, Wv = W[ab + a] * te.y;
+                        // merged form: the weight from the pattern's table (its
+                        // oscillatory factor -2 included)
+                        const bool mw = Pp->woff >= 0;
+                        const double Sv = S[ab + a] + te.x;
+                        const double Wv = mw ? w64_value(P->wt64[Pp->woff + (long long)(ab + a) * Pp->tm + e % Pp->tm])
+                                             : W[ab + a] * te.y;
                         double D;
-                        if (I->gk == SG_GK_OSC) D = -2.0 * sin(0.5 * Sv) * (V.sin_phi * cos(0.5 * Sv) + V.cos_phi * sin(0.5 * Sv));
+                        if (I->gk == SG_GK_OSC)
+                            D = (mw ? 1.0 : -2.0) * sin(0.5 * Sv) * (V.sin_phi * cos(0.5 * Sv) + V.cos_phi * sin(0.5 * Sv));
                         else D = expm1(Sv);
                         acc += Wv * D;
                         evals++;
@@ -421,6 +433,58 @@ void chk_xsum_adaptive(const double *v, long long n, int nthreads, double *out) 
         sg_x_plus(tot, acc[t]);
     }
     sg_x_pair(tot, Eb, &out[0], &out[1]);
+}
+
+// Every point of the merged form of (kind, d, L) with its weight from the
+// library's planner (merged_weights): X[n][d] coordinates on [0,1], Wt[n].
+// Returns the point count (only counted when it exceeds cap), -1 on error.
+long long chk_merged_points(int kind, int d, int L, double *X, double *Wt, long long cap) {
+    sg_rule_s rule;
+    rule.kind = kind;
+    rule.max_level = L + 2 > SG_MAX_LEVEL ? SG_MAX_LEVEL : L + 2;
+    std::vector<double> tx(2 * 4097 + 2), tw(2 * 4097 + 2);
+    for (int bk = 0; bk < 4; bk++)
+        for (int k = 1; k < rule.max_level; k++) {
+            int n = sg_block(kind, bk, k, tx.data(), tw.data());
+            rule.x[bk][k].assign(tx.begin(), tx.begin() + n);
+            rule.w[bk][k].assign(tw.begin(), tw.begin() + n);
+        }
+    std::vector<PatSpec> specs;
+    gen_patterns(SG_FORM_MERGED, d, L, specs);
+    drop_empty_patterns(&rule, specs);
+    Plan P;
+    if (!merged_weights(&rule, d, L, 1.0, specs, &P)) return -1;
+    long long n = 0;
+    for (const PatSpec &sp : specs) {
+        std::vector<int> ex(sp.r);
+        for (int t = 0; t < sp.r - 1; t++) ex[t] = sp.pre[t].k;
+        ex[sp.r - 1] = sp.tail.k;
+        std::vector<int> dir(sp.r);
+        for (int t = 0; t < sp.r; t++) dir[t] = t;
+        for (;;) {  // r-subsets in lexicographic order
+            // tuples: prefix digits with the last prefix position fastest, then the tail node
+            std::vector<int> j(sp.r, 0);
+            long long a = 0;
+            for (;;) {
+                if (n < cap) {
+                    for (int i = 0; i < d; i++) X[n * d + i] = 0.5;
+                    for (int t = 0; t < sp.r; t++) X[n * d + dir[t]] = rule.x[SG_BLK_NEW][ex[t]][j[t]];
+                    Wt[n] = w64_value(P.wt64[sp.woff + a]);
+                }
+                n++;
+                a++;
+                int t = sp.r - 1;
+                while (t >= 0 && ++j[t] == (int)rule.x[SG_BLK_NEW][ex[t]].size()) j[t--] = 0;
+                if (t < 0) break;
+            }
+            int t = sp.r - 1;
+            while (t >= 0 && dir[t] == d - sp.r + t) t--;
+            if (t < 0) break;
+            dir[t]++;
+            for (int u = t + 1; u < sp.r; u++) dir[u] = dir[u - 1] + 1;
+        }
+    }
+    return n;
 }
 
 // The single-integral fold's long accumulator (sg_lacc.h): v[0..n) split

@@ -80,7 +80,7 @@ CASES += [dict(name="d1", rule=2, fam=3, d=1, L=6, params=si.item_params(3, 1, 5
           dict(name="trap_slow", rule=1 | 16, fam=0, d=4, L=5, params=si.item_params(0, 4, 12))]
 
 
-@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("form", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c["name"])
 def test_fold_enumeration_matches_oracle(case, form):
     r = index_check.run(case["rule"], case["fam"], case["params"], case["d"], case["L"], form=form)
@@ -105,6 +105,16 @@ def test_chunking_does_not_change_the_sum(ppc, ctas, warps):
                         ctas_per_sm=ctas, warps=warps)
     assert r["violations"] == 0 and r["badpairs"] == 0
     assert _oracle_rel(c, r) < 1e-12
+
+
+def test_merged_form_evaluates_each_distinct_point_once():
+    # nested rules: the merged form's evaluations are the sparse grid's
+    # distinct points less the centre (the oracle counts them by merging)
+    for c in CASES:
+        if c["rule"] & 15 == 4:
+            continue
+        r = index_check.run(c["rule"], c["fam"], c["params"], c["d"], c["L"], form=4)
+        assert r["evals"] == oracle.count_distinct(c["rule"], c["d"], c["L"]) - 1
 
 
 def test_n_d_q_matches_oracle_count():
@@ -195,3 +205,37 @@ def test_divide_free_block_digits():
     # the prefix digits' q / m by a multiplier (Granlund-Montgomery) for every
     # block size up to 5000 nodes
     assert index_check.divmagic_mismatches(5000) == 0
+
+
+# ---------------------------------------------------------------------------
+# merged form (Eq. 2.8): every distinct point once with its merged weight
+# ---------------------------------------------------------------------------
+
+MERGED_CASES = [(2, 3, 4), (2, 5, 3), (4, 4, 4), (4, 3, 6), (3, 3, 3), (1, 4, 3), (2 | 16, 3, 5), (3 | 16, 2, 6),
+                (2, 1, 5), (4, 2, 1)]
+
+
+@pytest.mark.parametrize("kind,d,L", MERGED_CASES)
+def test_merged_weights_are_the_oracles_merged_point_weights(kind, d, L):
+    # the oracle's difference-form points with their product weights, added
+    # point by point, are the sparse grid's point weights (Eq. 2.8); the
+    # planner's merged weights (a different algorithm: generating series of
+    # the per-node difference weights, in double-double) must match them
+    import oracle
+    import index_check
+    Xo, Wo = oracle.points(kind, d, L, oracle.FORM_DIFF)
+    merged, mass = {}, {}
+    # the two sides build their nodes by different formulas: points are
+    # matched to 1e-12 (the nodes of these rules are at least 1e-4 apart)
+    for x, w in zip(map(tuple, np.round(Xo, 12)), Wo):
+        merged[x] = merged.get(x, 0.0) + w
+        mass[x] = mass.get(x, 0.0) + abs(w)
+    X, W = index_check.merged_points(kind, d, L)
+    centre = tuple([0.5] * d)
+    keys = [tuple(x) for x in np.round(X, 12)]
+    assert len(set(keys)) == len(keys)                     # each point once
+    assert set(keys) == set(merged) - {centre}             # every non-centre point
+    for k, w in zip(keys, W):
+        assert abs(w - merged[k]) <= 1e-13 * max(mass[k], 1.0), (k, w, merged[k])
+    # with the centre's weight the weights sum to the volume of the cube
+    assert abs(W.sum() + merged.get(centre, 0.0) - 1.0) <= 1e-12 * max(mass.values())

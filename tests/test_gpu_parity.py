@@ -23,11 +23,14 @@ import paper_2210_14313_gb300 as sg  # noqa: E402
 
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-6
+FF_TOL = 1e-9
 
 
 @pytest.fixture(scope="module")
 def rules():
-    return {k: sg.Rule(k, max_level=10) for k in (1, 2, 4)}
+    r = {k: sg.Rule(k, max_level=10) for k in (1, 2, 4)}
+    r[3] = sg.Rule(3, max_level=6)
+    return r
 
 
 def rel_err(r, o):
@@ -57,6 +60,32 @@ def test_fp64_configs(rules, c, form):
     assert rel_err(r, oracle_value(c)) <= FP64_TOL
 
 
+@pytest.mark.parametrize("prec", [sg.PREC_FP64, sg.PREC_FF])
+@pytest.mark.parametrize("c", CONFIGS + [dict(name="gp_L4", rule=3, fam=1, d=9, L=4, params=si.item_params(1, 9, 31)),
+                                         dict(name="trap_L5", rule=1, fam=2, d=6, L=5,
+                                              params=si.item_params(2, 6, 32))],
+                         ids=lambda c: c["name"])
+def test_merged_form(rules, c, prec):
+    # every distinct point once with its merged weight (Eq. 2.8): FP64 at the
+    # FP64 bar, float-float at its own, the evaluations the distinct points
+    r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec,
+                     form=sg.FORM_MERGED)
+    assert r.points == oracle.count_points(c["rule"], c["d"], c["L"])
+    assert rel_err(r, oracle_value(c)) <= (FP64_TOL if prec == sg.PREC_FP64 else FF_TOL)
+    if c["rule"] != 4:
+        assert r.evals == oracle.count_distinct(c["rule"], c["d"], c["L"]) - 1
+
+
+@pytest.mark.parametrize("c", [si.cfg3(si.FAM_PRODUCT_PEAK), si.cfg3(si.FAM_GAUSSIAN), si.cfg5(), si.cfg1()],
+                         ids=lambda c: c["name"])
+def test_mixed_merged_form(rules, c):
+    r = sg.integrate(rules[c["rule"]], c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=sg.PREC_MIXED,
+                     form=sg.FORM_MERGED)
+    err = rel_err(r, oracle_value(c))
+    assert err <= MIXED_TOL, (err, r)
+    assert err <= r.err_est
+
+
 @pytest.mark.parametrize("c", [si.cfg1(), si.cfg2()], ids=lambda c: c["name"])
 def test_fp64_combination_form(rules, c):
     # Eq. 2.6 literally; its binomial coefficients amplify rounding by the
@@ -73,14 +102,11 @@ def test_mixed_configs(rules, c):
                      prec=sg.PREC_MIXED)
     err = rel_err(r, oracle_value(c))
     assert err <= MIXED_TOL, (err, r)
-    assert err <= max(20 * r.err_est, 1e-7)  # the estimate is of the right size
+    assert err <= r.err_est  # the estimate bounds the error
 
 
-# Gauss-Legendre integrals in FP64 under SG_FORM_AUTO, which picks the
-# combination form where every coefficient C(d-1, L-k) is at most 1024
-# (fewer evaluations than the difference forms for a rule that is not
-# nested) and the telescoped form elsewhere: both sides of that boundary,
-# every family, against the oracle at the FP64 bar.
+# Gauss-Legendre integrals in FP64 under SG_FORM_AUTO (the merged form),
+# every family, from low to high d, against the oracle at the FP64 bar.
 AUTO_GL = [(d, L) for d, L in [(2, 8), (3, 7), (5, 6), (8, 5), (11, 6), (12, 6), (13, 6), (14, 5),
                                (14, 4), (20, 3), (33, 2), (46, 2), (200, 1), (7, 0)]]
 
@@ -95,11 +121,10 @@ def test_fp64_auto_form_gauss_legendre(rules, dL, fam):
     pts, ev = sg.count_points(rules[4], d, d + L)
     assert r.points == pts == oracle.count_points(4, d, L)
     assert r.evals == ev
-    comb = L >= 1 and max(math.comb(d - 1, j) for j in range(0, min(L, d - 1) + 1)) <= 1024
-    assert (ev <= pts) == comb or L == 0
-
-
-FF_TOL = 1e-9
+    # the merged form evaluates each distinct point once: no more than the
+    # n_d^q of Eq. 2.6 once d > L (for d <= L it also visits the points of the
+    # subgrids Eq. 2.6 leaves out, whose merged weights are zero)
+    assert ev <= pts or d <= L
 
 
 @pytest.mark.parametrize("c", CONFIGS, ids=lambda c: c["name"])
@@ -229,28 +254,49 @@ def test_mixed_guard(rules):
             assert err <= MIXED_TOL
 
 
-def test_batch_full_size_sampled(rules):
-    """The full 4096-item workload in one persistent launch (mixed precision,
-    no guard).  Every item is checked against the float64 separable DP: its
-    error must lie within the mixed bar or within the item's own error
-    estimate (items whose conditioning makes float evaluation miss 1e-6 are
-    the ones the guard recomputes in float-float, see test_mixed_guard);
-    the small items are also checked against the oracle."""
+def _dp_err(it, r):
+    rel, ls = dp_pin.smolyak_value_f64(it["rule"], it["fam"], it["params"], it["d"], it["L"])
+    if it["fam"] == si.FAM_OSCILLATORY:
+        return abs(r.value - rel) / abs(rel)
+    return abs(r.mant * math.exp(r.exp2 * math.log(2.0) - ls) - rel) / abs(rel)
+
+
+def test_batch_full_size_guarded(rules):
+    """The full 4096-item workload (d ~ U{5..200}, q - d ~ U{2..5}, four
+    families, two rules) in one persistent launch per precision tier: float
+    evaluation, the items whose error estimate exceeds 1e-6 / 4 recomputed in
+    float-float and what that still leaves above it in FP64.  Every item must
+    be within 1e-6 of the separable pin (a float64 evaluation of the same
+    Smolyak sum by a different algorithm, whose own error is far below that),
+    and the small ones within 1e-6 of the oracle."""
+    items = si.batch()
+    specs, pool = _batch(items, rules)
+    res = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED, guard_tol=MIXED_TOL / 4)
+    worst, checked = 0.0, 0
+    for it, r in zip(items, res):
+        err = _dp_err(it, r)
+        worst = max(worst, err)
+        assert err <= MIXED_TOL, (it["rule"], it["fam"], it["d"], it["L"], err, r.err_est)
+        if r.points <= 2e5 and checked < 64:
+            assert rel_err(r, oracle_value(it)) <= MIXED_TOL
+            checked += 1
+    assert checked >= 16
+    print("full batch, guarded: %.3f s, worst error %.2e" % (res[0].seconds, worst))
+
+
+def test_batch_full_size_float_estimate_bounds_the_error(rules):
+    """The same batch in float evaluation alone: the items badly enough
+    conditioned miss 1e-6 (the guard exists for them), but every item's error
+    stays below its own estimate, which is what the guard decides on."""
     items = si.batch()
     specs, pool = _batch(items, rules)
     res = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED)
-    checked = 0
+    above = 0
     for it, r in zip(items, res):
-        rel, ls = dp_pin.smolyak_value_f64(it["rule"], it["fam"], it["params"], it["d"], it["L"])
-        if it["fam"] == si.FAM_OSCILLATORY:
-            err = abs(r.value - rel) / abs(rel)
-        else:
-            err = abs(r.mant * math.exp(r.exp2 * math.log(2.0) - ls) - rel) / abs(rel)
-        assert err <= max(MIXED_TOL, 20 * r.err_est), (it["d"], it["L"], err, r.err_est)
-        if r.points <= 2e5 and checked < 64:
-            assert rel_err(r, oracle_value(it)) <= max(MIXED_TOL, 20 * r.err_est)
-            checked += 1
-    assert checked >= 16
+        err = _dp_err(it, r)
+        assert err <= r.err_est, (it["rule"], it["fam"], it["d"], it["L"], err, r.err_est)
+        above += err > MIXED_TOL
+    print("full batch, float only: %.3f s, %d of %d items above 1e-6" % (res[0].seconds, above, len(items)))
 
 
 # ---------------------------------------------------------------------------
@@ -312,6 +358,6 @@ def test_autotune_picks_a_grid_point_and_keeps_results(rules):
         assert sg.get_tuning(sg.PREC_MIXED) == best
         res = sg.integrate_batch(specs, pool, prec=sg.PREC_MIXED)
         for it, r in zip(items, res):
-            assert rel_err(r, oracle_value(it)) <= max(MIXED_TOL, 20 * r.err_est)
+            assert rel_err(r, oracle_value(it)) <= max(MIXED_TOL, r.err_est)
     finally:
         sg.set_tuning(sg.PREC_MIXED, *saved)
