@@ -36,7 +36,7 @@ METRIC = "effective sparse-grid points/sec and s/integral at stated rel. error v
 # summarised in profiles/sg_fold_kernel_d__cfg2_d12_gl_L6_oscillatory.txt.
 # Valid only for the kernel sources with this digest; otherwise reported as
 # null until the capture is taken again.
-_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (331264, "4789c59c20fc351d")}
+_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (331264, "91ca25a99c0d30b0")}
 _KERNEL_SOURCES = ["paper_2210_14313_gb300/csrc/sg_kernels.cu", "paper_2210_14313_gb300/csrc/sg_fold_logic.h",
                    "paper_2210_14313_gb300/csrc/sg_ff.cuh", "paper_2210_14313_gb300/csrc/sg_internal.h",
                    "paper_2210_14313_gb300/csrc/sg_reduce.cuh", "paper_2210_14313_gb300/csrc/sg_fixed.h",

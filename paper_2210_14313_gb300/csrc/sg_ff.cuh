@@ -1,6 +1,6 @@
 // Float-float ("FF") arithmetic for the fold: a value is an unevaluated sum
 // hi + lo of two floats with |lo| <= ulp(hi)/2, about 44 significant bits.
-// Everything runs on the FP32 pipes, which GB300 has at 64x the rate of its
+// Everything runs on the FP32 pipes, which GB300 has at 72x the rate of its
 // FP64 pipe.  The error-free transformations are Knuth's TwoSum and the
 // FMA-based TwoProduct (Dekker 1971 / Ogita, Rump & Oishi 2005); the
 // explicit __f*_rn intrinsics keep the compiler from contracting or

@@ -1,7 +1,7 @@
 // Double-precision sin, cos and expm1 of the FP64 fold, evaluated in 64-bit
 // fixed-point integer arithmetic.
 //
-// GB300 issues FP64 at 1/64 of the FP32 rate, while a 32 x 32 -> 64-bit
+// GB300 issues FP64 at 1/72 of the FP32 rate (measured), while a 32 x 32 -> 64-bit
 // integer multiply-add runs on the integer pipes at a much higher rate, so
 // the polynomial parts of the per-point deviation (Section 3's G evaluation)
 // are evaluated on integers: every intermediate is an unsigned magnitude
