@@ -495,6 +495,18 @@ def _extras(sg, oracle, torch, args):
                                "max_rel_err_vs_oracle": max(errs) if errs else None,
                                "oracle_checked_items": len(errs),
                                "max_err_est": max(r.err_est for r in res)}
+    # per-class chunk sizes tuned on this subset (sg_autotune_classes), then the
+    # guarded batch again with the table
+    try:
+        ncls = sg.autotune_classes(specs, pool, prec=1, reps=1)
+        sg.integrate_batch(specs, pool, prec=1, guard_tol=2.5e-7)
+        res = sg.integrate_batch(specs, pool, prec=1, guard_tol=2.5e-7)
+        errs = [_rel(res[k], o) for k, o in zip(small, refs)]
+        out["batch"]["mixed_guard_1e-6_class_tuned"] = {
+            "s": res[0].seconds, "points_per_s": pts / res[0].seconds, "classes": ncls,
+            "max_rel_err_vs_oracle": max(errs) if errs else None}
+    finally:
+        sg.tuning_clear()
     return out
 
 

@@ -315,6 +315,29 @@ SG_API sg_status sg_autotune(const sg_item *items, int n, const double *params_p
 
 
 /*
+ * Per-class tuning of the batch path (no counterpart in the paper; the
+ * paper's step sizes m and s of Algorithm 3.3 have no analogue on the GPU).
+ * A class is (family, rule, ceil(log2 d), q - d, precision).  For every class
+ * present in the items, sg_autotune_classes times the class's items as a
+ * batch (as sg_integrate_batch runs them, without the guard) under each
+ * candidate chunk size (1024, 4096, 16384, 65536, 262144 points per chunk),
+ * `reps` times after one warm-up, and keeps the fastest.  The table applies
+ * to every later sg_integrate_batch call in this process (the items of a
+ * class are planned with its chunk size; other items keep the precision's
+ * tuning) and is written to `path` as JSON unless path is NULL; *nclasses
+ * (may be NULL) receives the table's size.  sg_tuning_load replaces the
+ * table by one read from such a file; sg_tuning_clear empties it.  Chunk
+ * sizes change only the order in which terms are added: results agree to
+ * rounding.  Blocking.  Errors: SG_EINVAL (NULL, bad file), and those of
+ * sg_integrate_batch.
+ */
+SG_API sg_status sg_autotune_classes(const sg_item *items, int n, const double *params_pool,
+                                     int params_on_device, sg_precision prec, int reps, void *stream,
+                                     const char *path, int *nclasses);
+SG_API sg_status sg_tuning_load(const char *path, int *nclasses);
+SG_API sg_status sg_tuning_clear(void);
+
+/*
  * Measurement hooks (no counterpart in the paper).  sg_profile_begin starts
  * recording CUDA events around every fold-kernel launch this library
  * enqueues on `stream` (not inside graph replays); sg_profile_end

@@ -35,7 +35,7 @@ ABI_SYMBOLS = ["sg_rule_init", "sg_rule_init_growth", "sg_rule_destroy", "sg_rul
                "sg_status_string", "sg_get_tuning", "sg_set_tuning", "sg_autotune",
                "sg_profile_begin", "sg_profile_end", "sg_ceiling", "sg_integrate_noalloc",
                "sg_eval_functions", "sg_integrand_create", "sg_integrand_destroy", "sg_integrand_log",
-               "sg_integrate_user"]
+               "sg_integrate_user", "sg_autotune_classes", "sg_tuning_load", "sg_tuning_clear"]
 
 
 class SgError(RuntimeError):
@@ -96,6 +96,10 @@ def load(build_if_missing: bool = True):
     lib.sg_set_tuning.argtypes = [ip, ctypes.POINTER(sg_tuning)]
     lib.sg_autotune.argtypes = [ctypes.POINTER(sg_item), ip, vp, ip, ip, ip, vp,
                                 ctypes.POINTER(sg_tuning), ctypes.POINTER(ctypes.c_double)]
+    lib.sg_autotune_classes.argtypes = [ctypes.POINTER(sg_item), ip, vp, ip, ip, ip, vp, ctypes.c_char_p,
+                                        ctypes.POINTER(ctypes.c_int)]
+    lib.sg_tuning_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+    lib.sg_tuning_clear.argtypes = []
     lib.sg_profile_begin.argtypes = [vp]
     lib.sg_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.sg_ceiling.argtypes = [ip, ip, vp, ctypes.POINTER(ctypes.c_double)]
@@ -376,6 +380,39 @@ def autotune(specs, pool, prec: int = PREC_MIXED, reps: int = 3, stream=None):
                               _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)),
            "sg_autotune")
     return (t.points_per_chunk, t.ctas_per_sm, t.warps_per_cta), ms.value
+
+
+def autotune_classes(specs, pool, prec: int = PREC_MIXED, reps: int = 1, path=None, stream=None) -> int:
+    """Per-class chunk sizes for the batch path (sg_autotune_classes); returns
+    the number of classes in the table, which later batches use."""
+    arr = _items(specs)
+    try:
+        import torch
+        on_dev = isinstance(pool, torch.Tensor) and pool.is_cuda
+    except ImportError:
+        on_dev = False
+    if on_dev:
+        ptr, keep = ctypes.c_void_p(pool.data_ptr()), pool
+    else:
+        keep = np.ascontiguousarray(pool, dtype=np.float64)
+        ptr = ctypes.c_void_p(keep.ctypes.data)
+    n = ctypes.c_int(0)
+    _check(load().sg_autotune_classes(arr, len(specs), ptr, 1 if on_dev else 0, prec, reps,
+                                      _stream_handle(stream), path.encode() if path else None,
+                                      ctypes.byref(n)), "sg_autotune_classes")
+    del keep
+    return n.value
+
+
+def tuning_load(path) -> int:
+    """Loads a per-class table written by autotune_classes; returns its size."""
+    n = ctypes.c_int(0)
+    _check(load().sg_tuning_load(path.encode(), ctypes.byref(n)), "sg_tuning_load")
+    return n.value
+
+
+def tuning_clear():
+    _check(load().sg_tuning_clear(), "sg_tuning_clear")
 
 
 def profile_begin(stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -173,6 +174,28 @@ static sg_tuning g_tune[3] = {{2048, 4, 8}, {32768, 8, 4}, {32768, 8, 4}};
 
 static bool prec_ok(int p) { return p == SG_PREC_FP64 || p == SG_PREC_MIXED || p == SG_PREC_FF; }
 
+// Per-class chunk sizes of the batch path (sg_autotune_classes,
+// sg_tuning_load): a class is (family, rule kind, ceil(log2 d), q - d,
+// precision); its items are planned with the class's points per chunk.
+typedef std::tuple<int, int, int, int, int> ClassKey;
+static std::map<ClassKey, int> g_class_ppc;
+
+static int d_bucket(int d) {
+    int b = 0;
+    while ((1 << b) < d) b++;
+    return b;
+}
+
+static ClassKey class_key(const sg_item &it, int prec) {
+    return ClassKey(it.fam, it.rule->kind, d_bucket(it.d), it.q - it.d, prec);
+}
+
+// Requires g_mu held.
+static int class_ppc(const sg_item &it, int prec) {
+    auto f = g_class_ppc.find(class_key(it, prec));
+    return f == g_class_ppc.end() ? 0 : f->second;
+}
+
 extern "C" sg_status sg_get_tuning(sg_precision prec, sg_tuning *t) {
     if (!t || !prec_ok(prec)) return SG_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -315,8 +338,8 @@ struct PlanKey {
         if (reqs.size() != o.reqs.size()) return reqs.size() < o.reqs.size();
         for (size_t i = 0; i < reqs.size(); i++) {
             const Req &a = reqs[i], &b = o.reqs[i];
-            auto ta = std::make_tuple(a.rule, a.fam, a.d, a.L, a.form, a.param_off, a.grad);
-            auto tb = std::make_tuple(b.rule, b.fam, b.d, b.L, b.form, b.param_off, b.grad);
+            auto ta = std::make_tuple(a.rule, a.fam, a.d, a.L, a.form, a.param_off, a.grad, a.ppc);
+            auto tb = std::make_tuple(b.rule, b.fam, b.d, b.L, b.form, b.param_off, b.grad, b.ppc);
             if (ta != tb) return ta < tb;
         }
         return false;
@@ -931,6 +954,7 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
     ST(batch_reqs(items, n, prec, reqs, &pool));
     std::lock_guard<std::mutex> lk(g_mu);
     cudaGetLastError();  // a failed earlier call must not surface here
+    for (int k = 0; k < n; k++) reqs[k].ppc = class_ppc(items[k], prec);
     DevCtx *C = nullptr;
     ST(dev_ctx(&C));
     Plan *P = nullptr;
@@ -1159,5 +1183,111 @@ extern "C" sg_status sg_eval_functions(int kind, sg_precision prec, const double
     if (!prec_ok(prec)) return SG_EINVAL;
     cudaGetLastError();
     CK(sg_launch_fn(kind, prec, d_x, d_y, n, (cudaStream_t)stream));
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-class tuning of the batch path
+// ---------------------------------------------------------------------------
+
+static const int kClassCandidates[] = {1024, 4096, 16384, 65536, 262144};
+
+static sg_status write_class_table(const char *path) {
+    FILE *f = fopen(path, "w");
+    if (!f) return SG_EINVAL;
+    fprintf(f, "{\"classes\": [\n");
+    size_t i = 0;
+    for (auto &kv : g_class_ppc) {
+        fprintf(f, "  {\"family\": %d, \"rule\": %d, \"dbucket\": %d, \"L\": %d, \"prec\": %d, "
+                   "\"points_per_chunk\": %d}%s\n",
+                std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                std::get<4>(kv.first), kv.second, ++i < g_class_ppc.size() ? "," : "");
+    }
+    fprintf(f, "]}\n");
+    return fclose(f) == 0 ? SG_OK : SG_EINVAL;
+}
+
+extern "C" sg_status sg_autotune_classes(const sg_item *items, int n, const double *params_pool,
+                                         int params_on_device, sg_precision prec, int reps, void *stream,
+                                         const char *path, int *nclasses) {
+    if (!items || n < 1 || !params_pool || reps < 1 || !prec_ok(prec)) return SG_EINVAL;
+    std::map<ClassKey, std::vector<sg_item>> groups;
+    for (int k = 0; k < n; k++) {
+        if (!items[k].rule) return SG_EINVAL;
+        groups[class_key(items[k], prec)].push_back(items[k]);
+    }
+    std::vector<sg_result> res(n);
+    for (auto &g : groups) {
+        double best_t = 1e300;
+        int best = 0;
+        for (int ppc : kClassCandidates) {
+            {
+                std::lock_guard<std::mutex> lk(g_mu);
+                g_class_ppc[g.first] = ppc;
+            }
+            std::vector<double> ts;
+            for (int r = 0; r < reps + 1; r++) {
+                const sg_status st = sg_integrate_batch(g.second.data(), (int)g.second.size(), params_pool,
+                                                        params_on_device, prec, 0.0, stream, res.data());
+                if (st == SG_ERANGE) break;  // too many chunks at this size
+                if (st != SG_OK) {
+                    std::lock_guard<std::mutex> lk(g_mu);
+                    g_class_ppc.erase(g.first);
+                    return st;
+                }
+                if (r) ts.push_back(res[0].seconds);
+            }
+            if (ts.empty()) continue;
+            std::sort(ts.begin(), ts.end());
+            if (ts[ts.size() / 2] < best_t) {
+                best_t = ts[ts.size() / 2];
+                best = ppc;
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (best) g_class_ppc[g.first] = best;
+        else g_class_ppc.erase(g.first);
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (nclasses) *nclasses = (int)g_class_ppc.size();
+    return path ? write_class_table(path) : SG_OK;
+}
+
+// Reads the integer after "key": in s (a table line); false if absent.
+static bool json_int(const char *s, const char *key, int *v) {
+    char pat[64];
+    snprintf(pat, sizeof(pat), "\"%s\":", key);
+    const char *p = strstr(s, pat);
+    if (!p) return false;
+    return sscanf(p + strlen(pat), " %d", v) == 1;
+}
+
+extern "C" sg_status sg_tuning_load(const char *path, int *nclasses) {
+    if (!path) return SG_EINVAL;
+    FILE *f = fopen(path, "r");
+    if (!f) return SG_EINVAL;
+    std::map<ClassKey, int> table;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        int fam, rule, db, L, prec, ppc;
+        if (!strchr(line, '{') || !json_int(line, "family", &fam)) continue;
+        if (!json_int(line, "rule", &rule) || !json_int(line, "dbucket", &db) || !json_int(line, "L", &L) ||
+            !json_int(line, "prec", &prec) || !json_int(line, "points_per_chunk", &ppc) || ppc < 32 ||
+            !prec_ok(prec)) {
+            fclose(f);
+            return SG_EINVAL;
+        }
+        table[ClassKey(fam, rule, db, L, prec)] = ppc;
+    }
+    fclose(f);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_class_ppc = table;
+    if (nclasses) *nclasses = (int)table.size();
+    return SG_OK;
+}
+
+extern "C" sg_status sg_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_class_ppc.clear();
     return SG_OK;
 }

@@ -479,6 +479,9 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
         ItemBuild &b = ib[order[q]];
         const int g = b.role.integral;
         sg_rule rule = reqs[g].rule;
+        // a chunk size tuned for this integral's class replaces the plan's
+        const u64 item_target = reqs[g].ppc > 0 ? std::max<u64>((u64)reqs[g].ppc, 256) : target;
+        const u64 item_tail = reqs[g].ppc > 0 ? std::max<u64>(item_target / 4, 64) : tail_target;
         b.it.pat0 = (long long)P->pats.size();
         b.it.chunk0 = chunk;
         for (auto &sp : b.specs) {
@@ -525,18 +528,18 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
                 P->pat_chunk0.push_back(rec.chunk0);
             };
             const u64 pe = nsub * per_sub;
-            if (done >= tail_cut || tail_target == target) {
-                emit(0, nsub, done >= tail_cut ? tail_target : target);
+            if (done >= tail_cut || item_tail == item_target) {
+                emit(0, nsub, done >= tail_cut ? item_tail : item_target);
             } else if (done + pe > tail_cut) {
                 const u64 head = (tail_cut - done + per_sub - 1) / per_sub;  // subsets before the cut
                 if (head >= nsub) {
-                    emit(0, nsub, target);
+                    emit(0, nsub, item_target);
                 } else {
-                    emit(0, head, target);
-                    emit(head, nsub, tail_target);
+                    emit(0, head, item_target);
+                    emit(head, nsub, item_tail);
                 }
             } else {
-                emit(0, nsub, target);
+                emit(0, nsub, item_target);
             }
             done += pe;
         }
@@ -549,6 +552,10 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
         P->roles.push_back(b.role);
         P->item_integral.push_back(b.integral);
         if (b.role.role == SG_ROLE_FORWARD) P->integrals[g].flag_item = (int)q;
+    }
+    if (chunk > (1ull << 26)) {  // tuned chunk sizes too small for this plan
+        plan_free_host(P);
+        return SG_ERANGE;
     }
     P->nchunks = chunk;
     // items of each integral (the setup kernel's per-integral warp fills their values)

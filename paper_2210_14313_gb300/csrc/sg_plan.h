@@ -38,9 +38,10 @@ struct Req {
     int fam, d, L, form;
     long long param_off;
     int grad;
+    int ppc = 0;  // points per chunk for this integral (0: the precision's tuning)
     bool operator==(const Req &o) const {
         return rule == o.rule && fam == o.fam && d == o.d && L == o.L && form == o.form &&
-               param_off == o.param_off && grad == o.grad;
+               param_off == o.param_off && grad == o.grad && ppc == o.ppc;
     }
 };
 

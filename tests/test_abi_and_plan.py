@@ -239,3 +239,23 @@ def test_merged_weights_are_the_oracles_merged_point_weights(kind, d, L):
         assert abs(w - merged[k]) <= 1e-13 * max(mass[k], 1.0), (k, w, merged[k])
     # with the centre's weight the weights sum to the volume of the cube
     assert abs(W.sum() + merged.get(centre, 0.0) - 1.0) <= 1e-12 * max(mass.values())
+
+
+def test_class_tuning_table_loads_without_gpu(tmp_path):
+    # the per-class chunk-size table of the batch path is host data: its file
+    # round trip and its errors need no GPU
+    import ctypes
+    import paper_2210_14313_gb300 as sg
+    lib = sg.load()
+    p = tmp_path / "classes.json"
+    p.write_text('{"classes": [\n'
+                 '  {"family": 1, "rule": 4, "dbucket": 7, "L": 5, "prec": 1, "points_per_chunk": 16384},\n'
+                 '  {"family": 0, "rule": 2, "dbucket": 8, "L": 5, "prec": 0, "points_per_chunk": 4096}\n]}\n')
+    n = ctypes.c_int(0)
+    assert lib.sg_tuning_load(str(p).encode(), ctypes.byref(n)) == 0 and n.value == 2
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"classes": [{"family": 1, "rule": 4, "dbucket": 7, "L": 5, "prec": 7, '
+                   '"points_per_chunk": 16384}]}\n')
+    assert lib.sg_tuning_load(str(bad).encode(), ctypes.byref(n)) == 1          # bad precision
+    assert lib.sg_tuning_load(str(tmp_path / "none.json").encode(), ctypes.byref(n)) == 1
+    assert lib.sg_tuning_clear() == 0

@@ -347,6 +347,29 @@ def test_autograd_function(rules):
     assert torch.allclose(p.grad.cpu(), torch.tensor(3.0 * g), rtol=0, atol=1e-15 * np.abs(g).max())
 
 
+def test_autotune_classes_table_is_applied_and_changes_only_rounding(rules, tmp_path):
+    # per-class chunk sizes: the table is written, read back and applied to
+    # later batches, whose results agree with the untuned ones to rounding
+    items = si.batch(n=40, seed=22, d_hi=60, L_hi=4)
+    specs, pool = _batch(items, rules)
+    sg.tuning_clear()
+    try:
+        base = sg.integrate_batch(specs, pool, prec=sg.PREC_FP64)
+        path = str(tmp_path / "classes.json")
+        n = sg.autotune_classes(specs, pool, prec=sg.PREC_FP64, reps=1, path=path)
+        assert n > 0
+        text = open(path).read()
+        assert text.count("points_per_chunk") == n
+        sg.tuning_clear()
+        assert sg.tuning_load(path) == n
+        tuned = sg.integrate_batch(specs, pool, prec=sg.PREC_FP64)
+        for it, a, b in zip(items, base, tuned):
+            assert abs(b.mant * 2.0 ** (b.exp2 - a.exp2) - a.mant) <= 1e-14 * abs(a.mant)
+            assert rel_err(b, oracle_value(it)) <= FP64_TOL
+    finally:
+        sg.tuning_clear()
+
+
 def test_autotune_picks_a_grid_point_and_keeps_results(rules):
     items = si.batch(n=12, seed=21, d_hi=40, L_hi=3)
     specs, pool = _batch(items, rules)
