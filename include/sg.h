@@ -315,6 +315,38 @@ SG_API sg_status sg_autotune(const sg_item *items, int n, const double *params_p
 
 
 /*
+ * A batch split into shards (no counterpart in the paper; the paper runs on
+ * one CPU).  The subgrids of a batch are independent, so its chunk queue can
+ * be cut into nshards contiguous ranges, each run by its own call (on one
+ * GPU or, one process per GPU, on several).  sg_integrate_batch_shard runs
+ * shard `shard` of `nshards` of the same batch sg_integrate_batch would run
+ * (no guard; same planning) and returns, per item k (input order), the item's
+ * long accumulator over the shard's chunks in partials[k * SG_SHARD_LIMBS ..]
+ * (caller-owned host memory, n * SG_SHARD_LIMBS int64: the exact sum of the
+ * chunk sums as 32 carry-save limbs, then the absolute sum) and, in info[k]
+ * (caller-owned host, may be NULL), the item's values the combine needs.
+ * Every shard computes the same info.  sg_shard_combine adds the shards'
+ * limbs (integer additions: exact, in any order) and rounds and assembles
+ * each item as the kernels do, so the results are bitwise the same for every
+ * nshards, including 1, and the same as sg_integrate_batch's for the same
+ * items and precision.  The exchange between GPUs is the limbs: 512 bytes
+ * per item per shard.  Blocking.  Errors: SG_EINVAL (NULL, shard out of
+ * range), SG_ERANGE (nshards > 65536), and those of sg_integrate_batch.
+ */
+#define SG_SHARD_LIMBS 64
+typedef struct {
+    double mult, base_rel;      /* item value = mult (base_rel + T), relative to the scale */
+    double scale_m, scale_e2;   /* scale = scale_m 2^scale_e2 */
+    double unit_roundoff;       /* of the precision, for the error estimate */
+    uint64_t points, evals;
+} sg_shard_info;
+SG_API sg_status sg_integrate_batch_shard(const sg_item *items, int n, const double *params_pool,
+                                          int params_on_device, sg_precision prec, int shard, int nshards,
+                                          void *stream, long long *partials, sg_shard_info *info);
+SG_API sg_status sg_shard_combine(const long long *const *partials, int nshards, const sg_shard_info *info,
+                                  int n, sg_result *out);
+
+/*
  * Per-class tuning of the batch path (no counterpart in the paper; the
  * paper's step sizes m and s of Algorithm 3.3 have no analogue on the GPU).
  * A class is (family, rule, ceil(log2 d), q - d, precision).  For every class

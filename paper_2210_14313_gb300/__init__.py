@@ -35,7 +35,7 @@ ABI_SYMBOLS = ["sg_rule_init", "sg_rule_init_growth", "sg_rule_destroy", "sg_rul
                "sg_status_string", "sg_get_tuning", "sg_set_tuning", "sg_autotune",
                "sg_profile_begin", "sg_profile_end", "sg_ceiling", "sg_integrate_noalloc",
                "sg_eval_functions", "sg_integrand_create", "sg_integrand_destroy", "sg_integrand_log",
-               "sg_integrate_user", "sg_autotune_classes", "sg_tuning_load", "sg_tuning_clear"]
+               "sg_integrate_user", "sg_autotune_classes", "sg_tuning_load", "sg_tuning_clear", "sg_integrate_batch_shard", "sg_shard_combine"]
 
 
 class SgError(RuntimeError):
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(ctypes.c_int)]
     lib.sg_tuning_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     lib.sg_tuning_clear.argtypes = []
+    lib.sg_integrate_batch_shard.argtypes = [ctypes.POINTER(sg_item), ip, vp, ip, ip, ip, ip, vp, vp, vp]
+    lib.sg_shard_combine.argtypes = [ctypes.POINTER(ctypes.c_void_p), ip, vp, ip, ctypes.POINTER(sg_result)]
     lib.sg_profile_begin.argtypes = [vp]
     lib.sg_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.sg_ceiling.argtypes = [ip, ip, vp, ctypes.POINTER(ctypes.c_double)]
@@ -380,6 +382,49 @@ def autotune(specs, pool, prec: int = PREC_MIXED, reps: int = 3, stream=None):
                               _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)),
            "sg_autotune")
     return (t.points_per_chunk, t.ctas_per_sm, t.warps_per_cta), ms.value
+
+
+SHARD_LIMBS = 64
+
+
+class sg_shard_info(ctypes.Structure):
+    _fields_ = [("mult", ctypes.c_double), ("base_rel", ctypes.c_double), ("scale_m", ctypes.c_double),
+                ("scale_e2", ctypes.c_double), ("unit_roundoff", ctypes.c_double), ("points", ctypes.c_uint64),
+                ("evals", ctypes.c_uint64)]
+
+
+def integrate_batch_shard(specs, pool, shard: int, nshards: int, prec: int = PREC_FP64, stream=None):
+    """Shard `shard` of `nshards` of a batch (sg_integrate_batch_shard):
+    (partials as an int64 array [n, SHARD_LIMBS], info array)."""
+    arr = _items(specs)
+    try:
+        import torch
+        on_dev = isinstance(pool, torch.Tensor) and pool.is_cuda
+    except ImportError:
+        on_dev = False
+    if on_dev:
+        ptr, keep = ctypes.c_void_p(pool.data_ptr()), pool
+    else:
+        keep = np.ascontiguousarray(pool, dtype=np.float64)
+        ptr = ctypes.c_void_p(keep.ctypes.data)
+    parts = np.zeros((len(specs), SHARD_LIMBS), dtype=np.int64)
+    info = (sg_shard_info * len(specs))()
+    _check(load().sg_integrate_batch_shard(arr, len(specs), ptr, 1 if on_dev else 0, prec, shard, nshards,
+                                           _stream_handle(stream), ctypes.c_void_p(parts.ctypes.data),
+                                           ctypes.cast(info, ctypes.c_void_p)), "sg_integrate_batch_shard")
+    del keep
+    return parts, info
+
+
+def shard_combine(parts_list, info):
+    """Adds the shards' limbs exactly and assembles every item (sg_shard_combine)."""
+    parts_list = [np.ascontiguousarray(p, dtype=np.int64) for p in parts_list]
+    n = parts_list[0].shape[0]
+    ptrs = (ctypes.c_void_p * len(parts_list))(*[p.ctypes.data for p in parts_list])
+    res = (sg_result * n)()
+    _check(load().sg_shard_combine(ptrs, len(parts_list), ctypes.cast(info, ctypes.c_void_p), n, res),
+           "sg_shard_combine")
+    return [Result(r) for r in res]
 
 
 def autotune_classes(specs, pool, prec: int = PREC_MIXED, reps: int = 1, path=None, stream=None) -> int:

@@ -141,6 +141,7 @@ extern "C" sg_status sg_rule_init_growth(sg_rule_kind kind, sg_growth growth, in
 }
 
 static void plans_drop_rule(sg_rule r);
+static void drop_all_graphs();
 
 extern "C" sg_status sg_rule_destroy(sg_rule r) {
     if (!r) return SG_OK;
@@ -308,9 +309,11 @@ static sg_status plan_upload(Plan *P, const u64 *d_binom) {
 
 static sg_status build_plan(const std::vector<Req> &reqs, int prec, const sg_tuning &tune,
                             long long warps, const u64 *d_binom, Plan **out) {
+    static unsigned long long next_id = 0;
     Plan *P = nullptr;
     sg_status st = build_plan_host(reqs, prec, tune, warps, &P);
     if (st != SG_OK) return st;
+    P->id = ++next_id;
     st = plan_upload(P, d_binom);
     if (st != SG_OK) {
         plan_free(P);
@@ -347,7 +350,13 @@ struct PlanKey {
 };
 static std::map<PlanKey, Plan *> g_plans;
 
+// Cached graphs hold kernel parameters that point into plans' device memory:
+// every graph is dropped before any plan is freed.
 static void plans_drop_rule(sg_rule r) {
+    bool any = false;
+    for (auto &kv : g_plans)
+        for (auto &q : kv.first.reqs) any |= q.rule == r;
+    if (any) drop_all_graphs();
     for (auto it = g_plans.begin(); it != g_plans.end();) {
         bool uses = false;
         for (auto &q : it->first.reqs) uses |= q.rule == r;
@@ -381,6 +390,7 @@ static sg_status get_plan(const std::vector<Req> &reqs, int prec, Plan **out) {
     if (st != SG_OK) return st;
     if (g_plans.size() > 256) {  // bound the cache
         cudaDeviceSynchronize();
+        drop_all_graphs();
         for (auto &kv : g_plans) plan_free(kv.second);
         g_plans.clear();
     }
@@ -406,7 +416,7 @@ struct GraphEntry {
 struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
-    DevBuf tab32, tab64, tabff, slots, gslots, counters, flags, bases, vars, out, vout, grad, params, lacc;
+    DevBuf tab32, tab64, tabff, slots, gslots, counters, flags, bases, vars, out, vout, grad, params, lacc, ilacc;
     // the first 16 bytes of `counters` (work counter, finished-CTA count and
     // window flag of single-integral folds) and `lacc` are zero between
     // calls; false until a fresh allocation has been cleared
@@ -416,7 +426,7 @@ struct Workspace {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_join = nullptr;
     cudaStream_t own = nullptr;  // capture/replay stream of batch graphs (never the legacy stream)
     unsigned epoch = 0;
-    std::map<std::tuple<const Plan *, const double *, double, unsigned>, GraphEntry> graphs;
+    std::map<std::tuple<unsigned long long, const double *, double, unsigned>, GraphEntry> graphs;  // plan id
     // fold-kernel timing (sg_profile_begin / sg_profile_end)
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
@@ -446,6 +456,15 @@ static void drop_graphs(Workspace *W) {
         if (kv.second.g) cudaGraphDestroy(kv.second.g);
     }
     W->graphs.clear();
+}
+
+static void drop_all_graphs() {
+    for (auto &kv : g_ws) {
+        Workspace *W = kv.second;
+        cudaStreamSynchronize(W->stream);
+        if (W->own) cudaStreamSynchronize(W->own);
+        drop_graphs(W);
+    }
 }
 
 static sg_status get_ws(cudaStream_t s, Workspace **out) {
@@ -529,8 +548,17 @@ static double unit_roundoff(int prec) {
 // [u32 group tickets].
 static size_t counter_bytes(const Plan *P) { return 16 + 4 * (P->items.size() + P->ngroups); }
 
-// The launch's long accumulator of a single-integral fold (sum, absolute sum).
+// The launch's long accumulator of a single-integral fold (sum, absolute sum),
+// and one per item of a batch.
 static const size_t kLaccBytes = (size_t)2 * SG_LA_DIGITS * sizeof(long long);
+static const size_t kItemLaccBytes = kLaccBytes;
+
+// A contiguous range of a plan's chunk queue for one launch of a sharded
+// batch (sg_integrate_batch_shard): its items are not assembled.
+struct ShardRange {
+    unsigned long long lo = 0, hi = 0;  // hi 0: the whole queue
+    bool on = false;
+};
 
 // Makes every buffer a plan needs large enough (outside any capture).
 static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need64, bool needff,
@@ -540,6 +568,7 @@ static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need6
     if (needff) ST(ensure(W, W->tabff, (size_t)P->nentries * sizeof(float4)));
     ST(ensure(W, W->slots, (size_t)P->nchunks * sizeof(SgSlot)));
     ST(ensure(W, W->gslots, (size_t)P->ngroups * sizeof(SgGroupSlot)));
+    ST(ensure(W, W->ilacc, P->items.size() * kItemLaccBytes));
     ST(ensure(W, W->counters, counter_bytes(P)));
     ST(ensure(W, W->flags, 4 * P->items.size()));
     ST(ensure(W, W->bases, P->integrals.size() * sizeof(SgBaseDev)));
@@ -612,15 +641,19 @@ static cudaError_t launch_user_fold(const UserFold &uf, SgFoldArgs &fa, const Pl
 // capture, whose replays would not see the host's record of the counters).
 static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *d_params,
                           double guard_tol, SgOutDev *d_out, cudaStream_t s, const UserFold *uf = nullptr,
-                          bool single_ok = true) {
+                          bool single_ok = true, ShardRange shard = ShardRange()) {
     const int prec = P->prec;
     const int nitems = (int)P->items.size();
     SgOutDev *outp = d_out ? d_out : (SgOutDev *)W->out.p;
     // one forward integral: chunk sums go into per-CTA long accumulators and
     // the counters return to zero at the end of the fold, so no clearing
     // launch precedes it (except on fresh memory)
-    const bool single = single_ok && !uf && guard_tol == 0.0 && nitems == 1 && P->integrals.size() == 1 &&
-                        P->roles[0].role == SG_ROLE_FORWARD && P->nchunks > 0;
+    const bool single = single_ok && !shard.on && !uf && guard_tol == 0.0 && nitems == 1 &&
+                        P->integrals.size() == 1 && P->roles[0].role == SG_ROLE_FORWARD && P->nchunks > 0;
+    // the built-in folds of everything else add each chunk into its item's
+    // long accumulator (cleared before every fold launch)
+    const bool items_lacc = !single && !uf;
+    const size_t ilacc_bytes = (size_t)nitems * kItemLaccBytes;
     if (single) {
         if (!W->la_clean) {
             CK(cudaMemsetAsync(W->counters.p, 0, 16, s));
@@ -693,6 +726,11 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     fa.wtab = prec == 0 ? (const void *)P->d_wt64 : (const void *)P->d_wtff;
     fa.lacc = (long long *)W->lacc.p;
     fa.cta_done = (unsigned int *)((char *)W->counters.p + 8);
+    fa.ilacc = items_lacc ? (long long *)W->ilacc.p : nullptr;
+    fa.no_assemble = shard.on ? 1 : 0;
+    fa.chunk_lo = shard.lo;
+    fa.chunk_hi = shard.hi;
+    if (items_lacc) CK(cudaMemsetAsync(W->ilacc.p, 0, ilacc_bytes, s));
     CK(prof_mark(W, true, s));
     if (uf) CK(launch_user_fold(*uf, fa, P, C, s));
     else CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
@@ -703,6 +741,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
         // recomputed in float-float, which flags again those whose float-float
         // estimate still exceeds it; those are recomputed in FP64
         CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
+        CK(cudaMemsetAsync(W->ilacc.p, 0, ilacc_bytes, s));
         sa.tab32 = nullptr;
         sa.tabff = (float4 *)W->tabff.p;
         sa.flags = (int *)W->flags.p;
@@ -717,6 +756,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
         CK(sg_launch_fold(fa, 2, 0, fold_cfg(P, 2, C), s));
         CK(prof_mark(W, false, s));
         CK(cudaMemsetAsync(W->counters.p, 0, counter_bytes(P), s));
+        CK(cudaMemsetAsync(W->ilacc.p, 0, ilacc_bytes, s));
         sa.tabff = nullptr;
         sa.tab64 = (double2 *)W->tab64.p;
         CK(sg_launch_setup(sa, s));
@@ -976,7 +1016,7 @@ extern "C" sg_status sg_integrate_batch(const sg_item *items, int n, const doubl
         dp = (const double *)W->params.p;
     }
     // the launch sequence is captured once per (plan, params, guard) and replayed
-    auto key = std::make_tuple((const Plan *)P, dp, guard_tol, W->epoch);
+    auto key = std::make_tuple(P->id, dp, guard_tol, W->epoch);
     auto it = W->graphs.find(key);
     if (it == W->graphs.end()) {
         GraphEntry ge;
@@ -1289,5 +1329,73 @@ extern "C" sg_status sg_tuning_load(const char *path, int *nclasses) {
 extern "C" sg_status sg_tuning_clear(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_class_ppc.clear();
+    return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sharded batches
+// ---------------------------------------------------------------------------
+
+extern "C" sg_status sg_integrate_batch_shard(const sg_item *items, int n, const double *params_pool,
+                                              int params_on_device, sg_precision prec, int shard, int nshards,
+                                              void *stream, long long *partials, sg_shard_info *info) {
+    if (!params_pool || !partials || !prec_ok(prec)) return SG_EINVAL;
+    if (nshards < 1 || nshards > 65536) return nshards < 1 ? SG_EINVAL : SG_ERANGE;
+    if (shard < 0 || shard >= nshards) return SG_EINVAL;
+    std::vector<Req> reqs;
+    size_t pool = 0;
+    ST(batch_reqs(items, n, prec, reqs, &pool));
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaGetLastError();  // a failed earlier call must not surface here
+    for (int k = 0; k < n; k++) reqs[k].ppc = class_ppc(items[k], prec);
+    DevCtx *C = nullptr;
+    ST(dev_ctx(&C));
+    Plan *P = nullptr;
+    ST(get_plan(reqs, prec, &P));
+    Workspace *W = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    ST(get_ws(s, &W));
+    ST(ws_prepare(W, P, prec == SG_PREC_MIXED, prec == SG_PREC_FP64, prec == SG_PREC_FF,
+                  params_on_device ? 0 : pool));
+    const size_t nitems = P->items.size();
+    const size_t lbytes = nitems * kItemLaccBytes;
+    const size_t vbytes = nitems * sizeof(SgItemVar), bbytes = P->integrals.size() * sizeof(SgBaseDev);
+    ST(ensure_host(W, lbytes + vbytes + bbytes));
+    const double *dp = params_pool;
+    if (!params_on_device) {
+        CK(cudaMemcpyAsync(W->params.p, params_pool, pool * sizeof(double), cudaMemcpyHostToDevice, s));
+        dp = (const double *)W->params.p;
+    }
+    // this shard's contiguous range of the plan's chunk queue (an empty range
+    // starts at the end of the queue, where the kernel's first grab stops)
+    ShardRange r;
+    r.on = true;
+    r.lo = (unsigned long long)((unsigned __int128)P->nchunks * (unsigned)shard / (unsigned)nshards);
+    r.hi = (unsigned long long)((unsigned __int128)P->nchunks * (unsigned)(shard + 1) / (unsigned)nshards);
+    if (r.lo == r.hi) r.lo = r.hi = P->nchunks;
+    ST(run_plan(P, W, C, dp, 0.0, nullptr, s, nullptr, false, r));
+    unsigned char *h = (unsigned char *)W->h_pinned;
+    CK(cudaMemcpyAsync(h, W->ilacc.p, lbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + lbytes, W->vars.p, vbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + lbytes + vbytes, W->bases.p, bbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const long long *L = (const long long *)h;
+    const SgItemVar *V = (const SgItemVar *)(h + lbytes);
+    const SgBaseDev *B = (const SgBaseDev *)(h + lbytes + vbytes);
+    for (size_t q = 0; q < nitems; q++) {
+        const int g = P->item_integral[q];  // forward items only: the item of input g
+        if (g < 0 || P->roles[q].role != SG_ROLE_FORWARD) continue;
+        memcpy(partials + (size_t)g * SG_SHARD_LIMBS, L + q * SG_SHARD_LIMBS, SG_SHARD_LIMBS * sizeof(long long));
+        if (info) {
+            sg_shard_info &I = info[g];
+            I.mult = V[q].mult;
+            I.base_rel = V[q].base_rel;
+            I.scale_m = B[g].scale_m;
+            I.scale_e2 = B[g].scale_e2;
+            I.unit_roundoff = unit_roundoff(prec);
+            I.points = P->points[g];
+            I.evals = P->evals[g];
+        }
+    }
     return SG_OK;
 }

@@ -189,4 +189,14 @@ struct SgFoldArgs {
     // merged form: point weights of every pattern (SgW64 for the FP64 fold,
     // float pairs hi + lo for the float and float-float folds)
     const void *wtab;
+    // Batches and gradients (not single): when ilacc is set, every chunk adds
+    // its sum and absolute sum into its item's long accumulator
+    // (2 SG_LA_DIGITS limbs per item, zeroed before the launch) with integer
+    // atomics and counts itself in item_done; the warp that completes an
+    // item rounds and assembles it, unless no_assemble (a shard of a batch,
+    // whose items the host combines).  Without ilacc: the per-chunk slots.
+    long long *ilacc;
+    int no_assemble;
+    // chunks [chunk_lo, chunk_hi) of the plan's queue (chunk_hi 0: all)
+    unsigned long long chunk_lo, chunk_hi;
 };

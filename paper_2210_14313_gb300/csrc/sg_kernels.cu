@@ -558,7 +558,7 @@ __device__ __forceinline__ void la_warp_round(long long L, int lane, double &s, 
     const long long up = __shfl_up_sync(FULL_MASK, hi, 1);
     long long v = lane == 31 ? L : (long long)((unsigned long long)L & 0xffffffffull);
     if (lane > 0) v += up;
-    const double t = ldexp((double)v, 32 * lane + SG_LA_E0);
+    const double t = (double)v * sg_xs_double((unsigned long long)(32 * lane + SG_LA_E0 + 1023) << 52);
     const int E = warp_max_exp(sg_x_exp(t));
     SgX a = {0ull, 0ull};
     sg_x_add(a, t, E);
@@ -608,6 +608,46 @@ __device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la,
     }
 }
 
+// A finished chunk of a batch item (SgFoldArgs::ilacc): lane k adds digit k
+// of the chunk's sum (both parts) and absolute sum into the item's long
+// accumulator with integer atomics (at most three lanes of each are
+// non-zero), then the chunk counts itself; the warp that counts the item's
+// last chunk rounds the accumulator and assembles the item.  Integer
+// additions in any order give the same limbs, so the result does not depend
+// on which warp ran which chunk, nor on how the chunks were split over
+// launches (shards).
+__device__ __noinline__ void complete_chunk_item(const SgFoldArgs &A, int item, double vsum, double vlo,
+                                                 double vabs, int lane) {
+    long long *L = A.ilacc + (size_t)item * 2 * SG_LA_DIGITS;
+    int ovf = 0;
+    const long long d1 = sg_la_digit(vsum, lane, &ovf) + sg_la_digit(vlo, lane, &ovf);
+    const long long d2 = sg_la_digit(vabs, lane, &ovf);
+    // a term outside the window (or not finite) marks the absolute sum, which
+    // is otherwise never negative; the item then assembles as NaN
+    if (__any_sync(FULL_MASK, ovf) && lane == 0)
+        atomicAdd((unsigned long long *)&L[2 * SG_LA_DIGITS - 1], (unsigned long long)(-(1ll << 40)));
+    if (d1) atomicAdd((unsigned long long *)&L[lane], (unsigned long long)d1);
+    if (d2) atomicAdd((unsigned long long *)&L[SG_LA_DIGITS + lane], (unsigned long long)d2);
+    if (A.no_assemble) return;
+    __threadfence();
+    __syncwarp();
+    unsigned int ticket = 0;
+    if (lane == 0) ticket = ticket_add(A.item_done + item);
+    ticket = __shfl_sync(FULL_MASK, ticket, 0);
+    const SgItemDev *I = A.items + item;
+    if (ticket + 1ull != I->nchunk) return;
+    __syncwarp();
+    const long long Ls = __ldcg(L + lane), La = __ldcg(L + SG_LA_DIGITS + lane);
+    double s, c, as, ac;
+    la_warp_round(Ls, lane, s, c);
+    la_warp_round(La, lane, as, ac);
+    if (lane == 0) {
+        const double T = as + ac < 0.0 ? __longlong_as_double(0x7ff8000000000000ll) : s + c;
+        assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, A.guard_tol,
+                      A.unit_roundoff, item, T, as + ac);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     typedef typename PrefixState<T>::type PS;
@@ -624,11 +664,12 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         if (threadIdx.x == 0) s_flag[0] = 0;
         __syncthreads();
     }
+    const unsigned long long c_end = A.chunk_hi ? A.chunk_hi : A.nchunks;
     for (;;) {
         unsigned long long c = 0;
-        if (lane == 0) c = atomicAdd(A.work, 1ull);
+        if (lane == 0) c = A.chunk_lo + atomicAdd(A.work, 1ull);
         c = __shfl_sync(FULL_MASK, c, 0);
-        if (c >= A.nchunks) break;
+        if (c >= c_end) break;
         // pattern of chunk c: last pattern with chunk0 <= c
         long long lo = 0, hi = A.npat - 1;
         if (A.chunk_start) {
@@ -682,6 +723,10 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
             if (d1) atomicAdd((unsigned long long *)&s_la[lane], (unsigned long long)d1);
             if (d2) atomicAdd((unsigned long long *)&s_la[SG_LA_DIGITS + lane], (unsigned long long)d2);
             if (ovf) s_flag[0] = 1;
+            continue;
+        }
+        if (A.ilacc) {
+            complete_chunk_item(A, item, vsum, acc_lo, vabs, lane);
             continue;
         }
         if (lane == 0) {

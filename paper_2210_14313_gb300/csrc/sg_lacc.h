@@ -119,3 +119,27 @@ SG_XS void sg_la_round(long long *limb, double *s, double *c) {
     *s = neg ? -hs : hs;
     *c = neg ? -hc : hc;
 }
+
+// The value of 32 limbs as s + c by the rounding the kernels use when the
+// limbs are spread over a warp (one limb per lane): one carry step brings
+// every limb below 2^53 (the top limb keeps its carries), so that
+// limb_k * 2^(32k + SG_LA_E0) is an exact double; those 32 doubles are added
+// exactly in a 128-bit window under the largest of them (terms more than
+// 104 bits below it are cut towards zero) and rounded to s + c once.  The
+// host combine of sharded batches calls this, so that it rounds exactly as
+// the kernels do.
+SG_XS void sg_la_round_w(const long long *L, double *s, double *c) {
+    double t[SG_LA_DIGITS];
+    int E = 1;
+    for (int k = 0; k < SG_LA_DIGITS; k++) {
+        long long v = k == SG_LA_DIGITS - 1 ? L[k] : (long long)((unsigned long long)L[k] & 0xffffffffull);
+        if (k > 0) v += L[k - 1] >> 32;  // arithmetic shift: floor division by 2^32
+        // v * 2^(32k + SG_LA_E0), exact: |v| < 2^53 and the power of two is a normal double
+        t[k] = (double)v * sg_xs_double((unsigned long long)(32 * k + SG_LA_E0 + 1023) << 52);
+        const int e = sg_x_exp(t[k]);
+        E = e > E ? e : E;
+    }
+    SgX a = {0ull, 0ull};
+    for (int k = 0; k < SG_LA_DIGITS; k++) sg_x_add(a, t[k], E);
+    sg_x_pair(a, E, s, c);
+}

@@ -1,7 +1,9 @@
 // Host planner of libsg (see sg_plan.h).
 #include "sg_plan.h"
 #include "sg_rules.h"
+#include "sg_lacc.h"
 
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -604,3 +606,41 @@ void sg_fill_binomials(unsigned long long *B) {
         }
 }
 
+// The host combine of a sharded batch (include/sg.h): the shards' limbs added
+// as integers, then rounded (sg_la_round_w, the kernels' rounding) and
+// assembled with the same operations as the kernels' assemble_item, so that
+// every shard count gives the same bits.
+extern "C" sg_status sg_shard_combine(const long long *const *partials, int nshards, const sg_shard_info *info,
+                                      int n, sg_result *out) {
+    if (!partials || !info || !out || nshards < 1 || n < 1) return SG_EINVAL;
+    for (int k = 0; k < nshards; k++)
+        if (!partials[k]) return SG_EINVAL;
+    for (int k = 0; k < n; k++) {
+        long long L[SG_SHARD_LIMBS];
+        for (int j = 0; j < SG_SHARD_LIMBS; j++) {
+            unsigned long long v = 0;  // wrapping two's complement addition
+            for (int sh = 0; sh < nshards; sh++) v += (unsigned long long)partials[sh][(size_t)k * SG_SHARD_LIMBS + j];
+            L[j] = (long long)v;
+        }
+        double s, c, as, ac;
+        sg_la_round_w(L, &s, &c);
+        sg_la_round_w(L + SG_LA_DIGITS, &as, &ac);
+        const double AB = as + ac;
+        const double T = AB < 0.0 ? NAN : s + c;
+        const sg_shard_info &I = info[k];
+        const double rel = I.mult * (I.base_rel + T);
+        const double absrel = fabs(I.mult) * (fabs(I.base_rel) + AB);
+        int e1 = 0;
+        const double mant = frexp(I.scale_m * rel, &e1);
+        sg_result &r = out[k];
+        r.mant = mant;
+        r.exp2 = (int64_t)(I.scale_e2 + e1);
+        r.value = ldexp(mant, (int)(I.scale_e2 + e1));
+        r.cond = absrel / fabs(rel);
+        r.err_est = 0.05 * I.unit_roundoff * r.cond;
+        r.points = I.points;
+        r.evals = I.evals;
+        r.seconds = 0.0;
+    }
+    return SG_OK;
+}

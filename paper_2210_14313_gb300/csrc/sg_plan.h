@@ -46,6 +46,7 @@ struct Req {
 };
 
 struct Plan {
+    unsigned long long id = 0;  // unique per built plan (never reused, unlike its address)
     std::vector<Req> reqs;
     int prec = 0;
     sg_tuning tune{};

@@ -163,3 +163,14 @@ def merged_points(kind, d, L):
     W = np.zeros(n)
     lib.chk_merged_points(kind, d, L, X.ctypes.data_as(dp), W.ctypes.data_as(dp), n)
     return X, W
+
+
+def lacc_limbs(v):
+    """The 32 carry-save limbs of the long accumulator over v (as the kernels add chunk sums)."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_lacc_limbs.argtypes = [dp, ctypes.c_longlong, ctypes.c_void_p]
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(32, dtype=np.int64)
+    lib.chk_lacc_limbs(v.ctypes.data_as(dp), len(v), out.ctypes.data)
+    return out

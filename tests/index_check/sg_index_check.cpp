@@ -435,6 +435,15 @@ void chk_xsum_adaptive(const double *v, long long n, int nthreads, double *out) 
     sg_x_pair(tot, Eb, &out[0], &out[1]);
 }
 
+// The limbs of the long accumulator over v[0..n) (the kernels' per-item
+// accumulation: each term's digits added into carry-save limbs).
+void chk_lacc_limbs(const double *v, long long n, long long *limbs) {
+    int ovf = 0;
+    for (int k = 0; k < SG_LA_DIGITS; k++) limbs[k] = 0;
+    for (long long i = 0; i < n; i++)
+        for (int k = 0; k < SG_LA_DIGITS; k++) limbs[k] += sg_la_digit(v[i], k, &ovf);
+}
+
 // Every point of the merged form of (kind, d, L) with its weight from the
 // library's planner (merged_weights): X[n][d] coordinates on [0,1], Wt[n].
 // Returns the point count (only counted when it exceeds cap), -1 on error.

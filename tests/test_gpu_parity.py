@@ -347,6 +347,30 @@ def test_autograd_function(rules):
     assert torch.allclose(p.grad.cpu(), torch.tensor(3.0 * g), rtol=0, atol=1e-15 * np.abs(g).max())
 
 
+@pytest.mark.parametrize("prec", [sg.PREC_FP64, sg.PREC_MIXED])
+def test_batch_shards_combine_bitwise(rules, prec):
+    # the chunk queue cut into 1, 2 or 3 contiguous shards, each run by its own
+    # call; the combined limbs give the same bits for every shard count, and
+    # the same bits as the unsharded batch call
+    items = si.batch(n=32, seed=23, d_hi=50, L_hi=4)
+    specs, pool = _batch(items, rules)
+    whole = sg.integrate_batch(specs, pool, prec=prec)
+    bits = None
+    for K in (1, 2, 3):
+        parts, info = [], None
+        for k in range(K):
+            p, info = sg.integrate_batch_shard(specs, pool, k, K, prec=prec)
+            parts.append(p)
+        res = sg.shard_combine(parts, info)
+        b = [(r.mant, r.exp2, r.cond) for r in res]
+        assert bits is None or b == bits
+        bits = b
+    assert bits == [(r.mant, r.exp2, r.cond) for r in whole]
+    if prec == sg.PREC_FP64:
+        for it, r in zip(items, res):
+            assert rel_err(r, oracle_value(it)) <= FP64_TOL
+
+
 def test_autotune_classes_table_is_applied_and_changes_only_rounding(rules, tmp_path):
     # per-class chunk sizes: the table is written, read back and applied to
     # later batches, whose results agree with the untuned ones to rounding
