@@ -609,19 +609,15 @@ __device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la,
 }
 
 // A finished chunk of a batch item (SgFoldArgs::ilacc): lane k adds digit k
-// of the chunk's sum (both parts) and absolute sum into the item's long
-// accumulator with integer atomics (at most three lanes of each are
-// non-zero), then the chunk counts itself; the warp that counts the item's
-// last chunk rounds the accumulator and assembles the item.  Integer
-// additions in any order give the same limbs, so the result does not depend
-// on which warp ran which chunk, nor on how the chunks were split over
-// launches (shards).
-__device__ __noinline__ void complete_chunk_item(const SgFoldArgs &A, int item, double vsum, double vlo,
-                                                 double vabs, int lane) {
+// of the chunk's sum (d1) and absolute sum (d2) into the item's long
+// accumulator with integer atomics (a few lanes of each are non-zero), then
+// the chunk counts itself; the warp that counts the item's last chunk
+// rounds the accumulator and assembles the item.  Integer additions in any
+// order give the same limbs, so the result does not depend on which warp
+// ran which chunk, nor on how the chunks were split over launches (shards).
+__device__ __noinline__ void complete_chunk_item(const SgFoldArgs &A, int item, long long d1, long long d2,
+                                                 int ovf, int lane) {
     long long *L = A.ilacc + (size_t)item * 2 * SG_LA_DIGITS;
-    int ovf = 0;
-    const long long d1 = sg_la_digit(vsum, lane, &ovf) + sg_la_digit(vlo, lane, &ovf);
-    const long long d2 = sg_la_digit(vabs, lane, &ovf);
     // a term outside the window (or not finite) marks the absolute sum, which
     // is otherwise never negative; the item then assembles as NaN
     if (__any_sync(FULL_MASK, ovf) && lane == 0)
@@ -665,10 +661,19 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         __syncthreads();
     }
     const unsigned long long c_end = A.chunk_hi ? A.chunk_hi : A.nchunks;
+    // the first chunk of every warp is fixed (no atomic at the start, where all
+    // warps would contend for the counter at once; consecutive chunks, often
+    // alike in cost, go to different SMs); the later ones come from the counter
+    bool first = true;
     for (;;) {
         unsigned long long c = 0;
-        if (lane == 0) c = A.chunk_lo + atomicAdd(A.work, 1ull);
-        c = __shfl_sync(FULL_MASK, c, 0);
+        if (first) {
+            c = A.chunk_lo + (unsigned long long)warp * gridDim.x + blockIdx.x;
+        } else {
+            if (lane == 0) c = A.chunk_lo + (unsigned long long)gridDim.x * nw + atomicAdd(A.work, 1ull);
+            c = __shfl_sync(FULL_MASK, c, 0);
+        }
+        first = false;
         if (c >= c_end) break;
         // pattern of chunk c: last pattern with chunk0 <= c
         long long lo = 0, hi = A.npat - 1;
@@ -693,7 +698,54 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
             if (I->gk == SG_GK_OSC) fold_chunk<T, SG_GK_OSC, false>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
             else fold_chunk<T, SG_GK_EXPM1, false>(A, P, I, c, sP, sPos, sIdx, lane, F, waited);
         }
-        // the chunk's sum over the lanes, exact before one rounding
+        const double cf = P->coef;  // 1 for most patterns
+        if ((A.single || A.ilacc) && cf == 1.0) {
+            // the chunk's exact sum over the lanes (a 128-bit integer window,
+            // sg_xsum.h) and its absolute sum enter the long accumulators
+            // digit by digit: integer operations only, no rounding to doubles
+            SgX xs = {0ull, 0ull}, xm = {0ull, 0ull};
+            int Es, Em;
+            if constexpr (std::is_same<T, double>::value) {
+                if (P->woff >= 0 && A.wtab) {
+                    Es = warp_max_exp(F.xe);
+                    xs = F.xa;
+                    sg_x_shr(xs, Es - F.xe);
+                } else {
+                    Es = warp_max_exp(sg_x_exp(F.acc));
+                    sg_x_add(xs, F.acc, Es);
+                }
+                Em = Es;  // the FP64 fold skips |W D| per point: the chunk's |sum| stands in
+            } else {
+                const double v = std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa);
+                Es = warp_max_exp(sg_x_exp(v));
+                sg_x_add(xs, v, Es);
+                Em = warp_max_exp(sg_x_exp((double)F.habs));
+                sg_x_add(xm, (double)F.habs, Em);
+            }
+            warp_xadd(xs);
+            int ovf = 0;
+            long long m = 0;
+            const long long d1 = sg_la_x_digit(xs, Es, lane, &ovf, &m);
+            long long d2 = m;
+            if constexpr (!std::is_same<T, double>::value) {
+                warp_xadd(xm);
+                sg_la_x_digit(xm, Em, lane, &ovf, &m);
+                d2 = m;
+            }
+            if (A.single) {
+                // lane k adds digit k into the CTA's long accumulator (no two
+                // lanes share a limb)
+                if (d1) atomicAdd((unsigned long long *)&s_la[lane], (unsigned long long)d1);
+                if (d2) atomicAdd((unsigned long long *)&s_la[SG_LA_DIGITS + lane], (unsigned long long)d2);
+                if (ovf) s_flag[0] = 1;
+            } else {
+                complete_chunk_item(A, item, d1, d2, ovf, lane);
+            }
+            continue;
+        }
+        // other coefficients (the combination form's binomials) and the
+        // chunk-slot reduction: the chunk's sum over the lanes, exact before
+        // one rounding
         double acc, aabs, acc_lo = 0.0;
         if constexpr (std::is_same<T, double>::value) {
             // the FP64 fold skips |W D| per point: the chunk's |sum| stands in
@@ -711,22 +763,21 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
             acc = warp_sum(std::is_same<T, float>::value ? (double)F.hs + (double)F.hc : ff_to_double(F.fa));
             aabs = warp_sum((double)F.habs);
         }
-        const double cf = P->coef;  // 1 for most patterns: skip two dependent FP64 steps
         const double vsum = cf == 1.0 ? acc : acc * cf, vabs = cf == 1.0 ? aabs : aabs * fabs(cf);
-        if (A.single) {
-            // lane k adds digit k of the chunk's sum (both parts) and absolute
-            // sum into the CTA's long accumulator (at most three lanes of each
-            // are non-zero, and no two lanes share a limb)
+        const double vlo = cf == 1.0 ? acc_lo : acc_lo * cf;
+        if (A.single || A.ilacc) {
+            // lane k's digit of the chunk's sum (both parts) and absolute sum
+            // (at most three lanes of each are non-zero)
             int ovf = 0;
-            const long long d1 = sg_la_digit(vsum, lane, &ovf) + sg_la_digit(acc_lo, lane, &ovf);
+            const long long d1 = sg_la_digit(vsum, lane, &ovf) + sg_la_digit(vlo, lane, &ovf);
             const long long d2 = sg_la_digit(vabs, lane, &ovf);
-            if (d1) atomicAdd((unsigned long long *)&s_la[lane], (unsigned long long)d1);
-            if (d2) atomicAdd((unsigned long long *)&s_la[SG_LA_DIGITS + lane], (unsigned long long)d2);
-            if (ovf) s_flag[0] = 1;
-            continue;
-        }
-        if (A.ilacc) {
-            complete_chunk_item(A, item, vsum, acc_lo, vabs, lane);
+            if (A.single) {
+                if (d1) atomicAdd((unsigned long long *)&s_la[lane], (unsigned long long)d1);
+                if (d2) atomicAdd((unsigned long long *)&s_la[SG_LA_DIGITS + lane], (unsigned long long)d2);
+                if (ovf) s_flag[0] = 1;
+            } else {
+                complete_chunk_item(A, item, d1, d2, ovf, lane);
+            }
             continue;
         }
         if (lane == 0) {

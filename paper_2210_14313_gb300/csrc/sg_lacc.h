@@ -50,6 +50,38 @@ SG_XS long long sg_la_digit(double v, int k, int *ovf) {
     return (b >> 63) ? -(long long)dg : (long long)dg;
 }
 
+// Digit k of an exact 128-bit sum t whose unit is 2^(E - 1075 - SG_XG)
+// (sg_xsum.h): the 32 bits of |t| that fall in limb k, with the sign of t
+// (bits below the window are cut off towards zero, as sg_la_digit does for a
+// double); *mag gets the digit of |t|.  Sets *ovf when |t| reaches 2^447 or
+// when E marks an infinite or NaN term (E = 0x7ff).  A chunk's sum enters
+// the accumulator this way without being rounded to doubles first.
+SG_XS long long sg_la_x_digit(SgX t, int E, int k, int *ovf, long long *mag) {
+    const unsigned long long neg = t.hi >> 63;
+    if (neg) {
+        t.lo = ~t.lo + 1;
+        t.hi = ~t.hi + (t.lo == 0);
+    }
+    // bit i of |t| has weight 2^(u + i + SG_LA_E0) (u relative to the window)
+    const int u = E - 1075 - SG_XG - SG_LA_E0;
+    if (E >= 0x7ff) {
+        *ovf = 1;
+    } else if (t.hi | t.lo) {
+        const int p = t.hi ? 127 - sg_xs_clz(t.hi) : 63 - sg_xs_clz(t.lo);  // top bit
+        if (u + p > 32 * SG_LA_DIGITS - 2) *ovf = 1;
+    }
+    const int o = 32 * k - u;  // digit k holds bits o .. o + 31 of |t|
+    unsigned long long dg;
+    if (o >= 128 || o <= -32) dg = 0;
+    else if (o >= 64) dg = t.hi >> (o - 64);
+    else if (o > 0) dg = (t.lo >> o) | (t.hi << (64 - o));
+    else if (o == 0) dg = t.lo;
+    else dg = t.lo << -o;
+    dg &= 0xffffffffull;
+    *mag = (long long)dg;
+    return neg ? -(long long)dg : (long long)dg;
+}
+
 // Index of the lowest digit that can be non-zero for v (its non-zero digits
 // lie in k0 .. k0 + 2), or -1 when v has no bits inside the window; sets
 // *ovf for terms above it, infinities and NaNs.

@@ -298,6 +298,109 @@ bool count_points(int kind, int d, int L, u64 *out) {
     return true;
 }
 
+// Run-aware chunks.  The fold walks a chunk's subsets in runs that share
+// their first r - 1 directions (the last direction takes every value after
+// the prefix's last one), and every run costs at least one warp pass of 32
+// lanes plus its prefix fold, however few points it has.  Where runs are
+// short (d small against r, or the ends of each prefix's stretch) a chunk
+// sized by points alone can hold a dozen runs and take several times as
+// long as its neighbours, and in a single integral, whose chunks are about
+// one per resident warp, the slowest chunk sets the time.  So for single
+// integrals the runs are walked here, on the host, the chunks are sized by
+// the lane slots they occupy (passes x 32 plus a prefix fold per run and
+// prefix block), and runs are cut between subsets where needed.
+
+// Lane slots of k subsets of one run of a pattern with A prefix tuples and
+// tm tail nodes (k * tm tail entries per prefix tuple).
+static u64 run_slots(u64 A, u64 tm, u64 k) {
+    const u64 kPrefixSlots = 16;  // a prefix fold: about half a pass
+    u64 c = 0;
+    for (u64 b = 0; b * SG_APAD < A; b++) {
+        const u64 At = std::min<u64>(SG_APAD, A - b * SG_APAD);
+        c += 32 * ((At * k * tm + 31) / 32) + kPrefixSlots;
+    }
+    return c;
+}
+
+// Calls fn(len) for the runs of the r-subsets of d directions in the
+// fold's order: prefix tuples p_0 < .. < p_{r-2} <= d - 2 in lexicographic
+// order, each followed by d - 1 - p_{r-2} subsets (r = 1: one run of d).
+template <class F> static void for_each_run(int d, int r, F fn) {
+    if (r == 1) {
+        fn((u64)d);
+        return;
+    }
+    std::vector<int> p(r - 1);
+    for (int t = 0; t < r - 1; t++) p[t] = t;
+    for (;;) {
+        fn((u64)(d - 1 - p[r - 2]));
+        int t = r - 2;
+        while (t >= 0 && p[t] >= d - 2 - (r - 2 - t)) t--;
+        if (t < 0) return;
+        p[t]++;
+        for (int u = t + 1; u < r - 1; u++) p[u] = p[u - 1] + 1;
+    }
+}
+
+// Chunks of one pattern whose subsets need no splitting, each closed when
+// its lane slots would pass `budget`; consecutive chunks of equal size share
+// one record (the last chunk of a record may be smaller).  With P null the
+// chunks are only counted.  Returns the number of chunks.
+static u64 chunk_by_runs(const SgPatDev &pd, int d, u64 budget, u64 &chunk, Plan *P) {
+    const u64 A = (u64)pd.A, tm = (u64)pd.tm;
+    std::vector<u64> sizes;  // subsets per chunk
+    u64 cur = 0, cur_n = 0;
+    auto close = [&]() {
+        sizes.push_back(cur_n);
+        cur = 0;
+        cur_n = 0;
+    };
+    for_each_run(d, pd.r, [&](u64 m) {
+        while (m > 0) {
+            if (cur + run_slots(A, tm, m) <= budget) {
+                cur += run_slots(A, tm, m);
+                cur_n += m;
+                return;
+            }
+            // the most subsets of this run that still fit (at least one in an empty chunk)
+            u64 lo = 0, hi = m;
+            while (lo < hi) {
+                const u64 mid = (lo + hi + 1) / 2;
+                if (cur + run_slots(A, tm, mid) <= budget) lo = mid;
+                else hi = mid - 1;
+            }
+            if (lo == 0 && cur_n == 0) lo = 1;
+            if (lo > 0) {
+                cur += run_slots(A, tm, lo);
+                cur_n += lo;
+                m -= lo;
+            }
+            close();
+        }
+    });
+    if (cur_n) close();
+    if (!P) return sizes.size();
+    u64 rank = 0;
+    for (size_t i = 0; i < sizes.size();) {
+        size_t j = i + 1;
+        while (j < sizes.size() && sizes[j] == sizes[i]) j++;
+        if (j < sizes.size() && sizes[j] < sizes[i]) j++;
+        SgPatDev rec = pd;
+        rec.rank0 = rank;
+        for (size_t k = i; k < j; k++) rank += sizes[k];
+        rec.nsub = rank;
+        rec.chunk0 = chunk;
+        rec.asplit = 1;
+        rec.ablk = pd.A;
+        rec.spc = sizes[i];
+        chunk += j - i;
+        P->pats.push_back(rec);
+        P->pat_chunk0.push_back(rec.chunk0);
+        i = j;
+    }
+    return sizes.size();
+}
+
 struct ItemBuild {
     SgItemDev it;
     SgItemRole role;
@@ -471,10 +574,75 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     if (total / target > max_chunks) target = total / max_chunks + 1;
     // guided tail: the last eighth of the queue gets chunks of a quarter of
     // the size, so that the warps drain it together instead of waiting for
-    // a few full-size chunks grabbed last
+    // a few full-size chunks grabbed last; but no tail chunk below four warp
+    // passes, whose fixed work would outweigh their points
     const u64 tail_cut = total - total / 8;
-    u64 tail_target = std::max<u64>(target / 4, 16);
+    u64 tail_target = std::min<u64>(target, std::max<u64>(target / 4, 128));
     if (total / tail_target > max_chunks) tail_target = target;
+    // single integrals (no class tuning, the chunk size set by the warp count
+    // rather than the tuned maximum): run-aware chunks sized by lane slots,
+    // about one per resident warp, for every pattern whose runs can be walked
+    // within a budget of 2^22 runs per plan
+    bool by_runs = target < (u64)tune.points_per_chunk;
+    for (const Req &R : reqs) by_runs = by_runs && R.ppc == 0;
+    std::vector<std::vector<char>> use_runs(ib.size());
+    u64 slot_budget = 0;
+    if (by_runs) {
+        unsigned __int128 run_budget = (unsigned __int128)1 << 22;
+        u64 slots = 0;
+        auto pattern_shape = [&](const ItemBuild &b, const PatSpec &sp, SgPatDev &pd) {
+            sg_rule rule = reqs[b.role.integral].rule;
+            memset(&pd, 0, sizeof(pd));
+            pd.r = sp.r;
+            pd.A = 1;
+            for (int t = 0; t < sp.r - 1; t++) pd.A *= tab_m(rule, sp.pre[t]);
+            pd.tm = tab_m(rule, sp.tail);
+        };
+        for (size_t q = 0; q < order.size(); q++) {
+            ItemBuild &b = ib[order[q]];
+            use_runs[order[q]].assign(b.specs.size(), 0);
+            for (size_t k = 0; k < b.specs.size(); k++) {
+                const PatSpec &sp = b.specs[k];
+                const u64 nsub = (u64)binom128(b.it.d, sp.r);
+                if (nsub == 0) continue;
+                SgPatDev pd;
+                pattern_shape(b, sp, pd);
+                const unsigned __int128 runs = sp.r == 1 ? 1 : binom128(b.it.d - 1, sp.r - 1);
+                if (runs <= run_budget) {
+                    run_budget -= runs;
+                    use_runs[order[q]][k] = 1;
+                    for_each_run(b.it.d, sp.r, [&](u64 m) { slots += run_slots((u64)pd.A, (u64)pd.tm, m); });
+                } else {
+                    slots += nsub * (u64)pd.A * (u64)pd.tm;
+                }
+            }
+        }
+        // the smallest budget whose chunks (each pattern cut separately, each
+        // chunk filled up to whole passes) number no more than the warps
+        auto count = [&](u64 budget) {
+            u64 n = 0;
+            for (size_t q = 0; q < order.size(); q++) {
+                ItemBuild &b = ib[order[q]];
+                for (size_t k = 0; k < b.specs.size(); k++) {
+                    if (!use_runs[order[q]][k]) continue;
+                    SgPatDev pd;
+                    pattern_shape(b, b.specs[k], pd);
+                    if (run_slots((u64)pd.A, (u64)pd.tm, 1) > budget) return ~0ull;
+                    u64 none = 0;
+                    n += chunk_by_runs(pd, b.it.d, budget, none, nullptr);
+                }
+            }
+            return n;
+        };
+        u64 lo = std::max<u64>(slots / warps + 1, 48), hi = lo;
+        while (count(hi) > warps && hi < (1ull << 40)) hi *= 2;
+        while (lo < hi) {  // the count does not grow with the budget
+            const u64 mid = lo + (hi - lo) / 2;
+            if (count(mid) <= warps) hi = mid;
+            else lo = mid + 1;
+        }
+        slot_budget = lo;
+    }
     u64 done = 0;
     u64 chunk = 0;
     for (size_t q = 0; q < order.size(); q++) {
@@ -486,7 +654,8 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
         const u64 item_tail = reqs[g].ppc > 0 ? std::max<u64>(item_target / 4, 64) : tail_target;
         b.it.pat0 = (long long)P->pats.size();
         b.it.chunk0 = chunk;
-        for (auto &sp : b.specs) {
+        for (size_t ks = 0; ks < b.specs.size(); ks++) {
+            const PatSpec &sp = b.specs[ks];
             SgPatDev pd;
             memset(&pd, 0, sizeof(pd));
             pd.item = (int)q;
@@ -530,6 +699,11 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
                 P->pat_chunk0.push_back(rec.chunk0);
             };
             const u64 pe = nsub * per_sub;
+            if (by_runs && use_runs[order[q]][ks] && run_slots(A, (u64)pd.tm, 1) <= slot_budget) {
+                chunk_by_runs(pd, b.it.d, slot_budget, chunk, P);
+                done += pe;
+                continue;
+            }
             if (done >= tail_cut || item_tail == item_target) {
                 emit(0, nsub, done >= tail_cut ? item_tail : item_target);
             } else if (done + pe > tail_cut) {

@@ -56,7 +56,7 @@ __device__ inline void assemble_item(const SgItemDev *items, const SgItemVar *va
 // any order; the total is rounded once to a pair (s, c).
 __device__ __forceinline__ int warp_max_exp(int e) { return (int)__reduce_max_sync(SG_FULL_MASK, (unsigned)e); }
 
-__device__ __forceinline__ void warp_xsum(SgX a, int E, double &s, double &c) {
+__device__ __forceinline__ void warp_xadd(SgX &a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         SgX b;
@@ -64,6 +64,10 @@ __device__ __forceinline__ void warp_xsum(SgX a, int E, double &s, double &c) {
         b.hi = __shfl_xor_sync(SG_FULL_MASK, a.hi, o);
         sg_x_plus(a, b);
     }
+}
+
+__device__ __forceinline__ void warp_xsum(SgX a, int E, double &s, double &c) {
+    warp_xadd(a);
     sg_x_pair(a, E, &s, &c);
 }
 

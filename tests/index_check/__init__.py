@@ -149,6 +149,18 @@ def lacc(v, nparts=1):
     return out[0], out[1], int(out[2])
 
 
+def lacc_x(v, nparts=1):
+    """(s, c, overflow, |sum| of the parts) of the long accumulator fed with
+    the exact 128-bit window sums of nparts parts of v (sg_la_x_digit)."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_lacc_x.argtypes = [dp, ctypes.c_longlong, ctypes.c_int, dp]
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(4)
+    lib.chk_lacc_x(v.ctypes.data_as(dp), len(v), nparts, out.ctypes.data_as(dp))
+    return out[0], out[1], int(out[2]), out[3]
+
+
 def merged_points(kind, d, L):
     """Every point of the merged form (distinct points of the sparse grid
     except the centre) with the planner's merged weight: (X[n, d], W[n])."""

@@ -522,4 +522,30 @@ void chk_lacc(const double *v, long long n, int nparts, double *out) {
     out[2] = ovf;
 }
 
+// The long accumulator fed as the kernels feed it a chunk's exact sum:
+// the terms are cut into nparts chunks, each chunk's terms are added exactly
+// in a 128-bit window under its largest term (sg_xsum.h) and the window
+// sum enters the limbs digit by digit (sg_la_x_digit) without a rounding
+// to doubles.  out = (s, c, overflow, sum of |chunk sums| as s).
+void chk_lacc_x(const double *v, long long n, int nparts, double *out) {
+    std::vector<long long> tot(SG_LA_DIGITS, 0), mag(SG_LA_DIGITS, 0);
+    int ovf = 0;
+    for (int p = 0; p < nparts; p++) {
+        const long long i0 = n * p / nparts, i1 = n * (p + 1) / nparts;
+        int E = 1;
+        for (long long i = i0; i < i1; i++) E = sg_x_exp(v[i]) > E ? sg_x_exp(v[i]) : E;
+        SgX t = {0ull, 0ull};
+        for (long long i = i0; i < i1; i++) sg_x_add(t, v[i], E);
+        for (int k = 0; k < SG_LA_DIGITS; k++) {
+            long long m = 0;
+            tot[k] += sg_la_x_digit(t, E, k, &ovf, &m);
+            mag[k] += m;
+        }
+    }
+    double mc = 0.0;
+    sg_la_round(tot.data(), &out[0], &out[1]);
+    sg_la_round(mag.data(), &out[3], &mc);
+    out[2] = ovf;
+}
+
 }  // extern "C"

@@ -96,3 +96,50 @@ def test_long_accumulator_window_ends():
     assert index_check.lacc(np.array([1.0, float("inf")]))[2] == 1
     assert index_check.lacc(np.array([1.0, float("nan")]))[2] == 1
     assert index_check.lacc(np.array([0.0, -0.0])) == (0.0, 0.0, 0)
+
+
+@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("nparts", [1, 4, 37])
+def test_long_accumulator_fed_exact_window_sums(k, nparts):
+    # each part's terms lie within 40 binades, so its 128-bit window sum is
+    # exact and enters the limbs digit by digit without rounding: the total
+    # is the exact sum, the same as with the terms fed one by one
+    v = list(_cases())[k]
+    s, c, ovf, amag = index_check.lacc_x(v, nparts)
+    assert ovf == 0
+    ex = _exact(v)
+    assert s == float(ex)
+    assert abs(Fraction(s) + Fraction(c) - ex) <= abs(ex) * Fraction(2) ** -96
+    assert (s, c) == index_check.lacc(v, nparts)[:2]
+    parts = [_exact(v[len(v) * p // nparts:len(v) * (p + 1) // nparts]) for p in range(nparts)]
+    # (rounded once: ties away from zero, so within half an ulp)
+    mag = sum(abs(x) for x in parts)
+    assert abs(Fraction(amag) - mag) <= mag * Fraction(2) ** -53
+
+
+def test_exact_window_digits_at_every_offset():
+    # one term per part, its unit stepping through every offset of the
+    # 32-bit digit grid (and across the ends of the 128-bit window sum)
+    rng = np.random.default_rng(9)
+    for e in range(-500, 420, 7):  # terms keep all their bits above 2^-576
+        v = rng.standard_normal(3) * 2.0 ** e
+        s, c, ovf, _ = index_check.lacc_x(v, 3)
+        assert ovf == 0
+        # exact: the sum of three terms has at most 55 bits (a tie between two
+        # doubles rounds away from zero)
+        assert Fraction(s) + Fraction(c) == _exact(v)
+        assert abs(Fraction(s) - _exact(v)) <= abs(_exact(v)) * Fraction(2) ** -53
+        assert index_check.lacc_x(-v, 3)[:2] == (-s, -c)
+
+
+def test_exact_window_digits_window_ends():
+    # below 2^-576 a part's sum is cut towards zero; from 2^447 on, and for
+    # infinite or NaN terms, the overflow flag is set
+    assert index_check.lacc_x(np.array([1.0, 2.0 ** -600]), 2)[:2] == (1.0, 0.0)
+    assert index_check.lacc_x(np.array([2.0 ** -570, 2.0 ** -600]), 2)[:2] == (2.0 ** -570, 0.0)
+    assert index_check.lacc_x(np.array([1.0, 2.0 ** 447]), 2)[2] == 1
+    assert index_check.lacc_x(np.array([2.0 ** 446, 2.0 ** 446]), 1)[2] == 1   # the part's sum is 2^447
+    assert index_check.lacc_x(np.array([2.0 ** 446, 2.0 ** 445]), 1)[2] == 0
+    assert index_check.lacc_x(np.array([1.0, float("inf")]), 1)[2] == 1
+    assert index_check.lacc_x(np.array([1.0, float("nan")]), 2)[2] == 1
+    assert index_check.lacc_x(np.array([0.0, -0.0]), 1)[:3] == (0.0, 0.0, 0)
