@@ -570,38 +570,62 @@ __device__ __forceinline__ void la_warp_round(long long L, int lane, double &s, 
 // integer atomics (the order of the additions cannot change the sum, so the
 // result does not depend on which CTA ran which chunk); the last CTA to
 // finish rounds it, assembles the output record and returns the launch's
-// accumulator and counters to zero for the next launch.
-__device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la, int *s_flag) {
+// accumulator and counters to zero for the next launch.  Everything here is
+// latency on the path of every call: the sum and the absolute sum are
+// rounded by two warps side by side, and the values the assembly needs are
+// loaded while they do.
+__device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la, int *s_flag, double *s_r) {
     const int NL = 2 * SG_LA_DIGITS;
     __syncthreads();
-    if ((int)threadIdx.x < NL) {
-        const long long v = s_la[threadIdx.x];
-        if (v) atomicAdd((unsigned long long *)&A.lacc[threadIdx.x], (unsigned long long)v);
+    for (int k = threadIdx.x; k < NL; k += blockDim.x) {
+        const long long v = s_la[k];
+        if (v) atomicAdd((unsigned long long *)&A.lacc[k], (unsigned long long)v);
     }
-    __threadfence();
+    if (threadIdx.x == 0 && s_flag[0]) atomicOr(A.cta_done + 1, 1u);
+    __threadfence();  // this CTA's additions before its count (one fence serves both)
     __syncthreads();
+    if (threadIdx.x == 0) s_flag[1] = atomicAdd(A.cta_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    // two warps: warp 0 holds the sum's limbs, warp 1 the absolute sum's (a
+    // one-warp CTA rounds both in turn)
+    const bool two = blockDim.x >= 64;
+    if (!s_flag[1] || (int)threadIdx.x >= (two ? NL : 32)) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31;
+    const long long L = __ldcg(A.lacc + threadIdx.x);
+    A.lacc[threadIdx.x] = 0;
+    long long La = 0;
+    if (!two) {
+        La = __ldcg(A.lacc + SG_LA_DIGITS + lane);
+        A.lacc[SG_LA_DIGITS + lane] = 0;
+    }
+    SgItemVar V;
+    SgBaseDev B;
+    int g = 0;
+    long long oi = 0;
+    bool ovf = false;
     if (threadIdx.x == 0) {
-        if (s_flag[0]) atomicOr(A.cta_done + 1, 1u);
-        __threadfence();
-        s_flag[1] = atomicAdd(A.cta_done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_flag[1] || threadIdx.x >= 32) return;
-    __threadfence();
-    const int lane = threadIdx.x;
-    const long long Ls = __ldcg(A.lacc + lane), La = __ldcg(A.lacc + SG_LA_DIGITS + lane);
-    A.lacc[lane] = 0;
-    A.lacc[SG_LA_DIGITS + lane] = 0;
-    double s, c, as, ac;
-    la_warp_round(Ls, lane, s, c);
-    la_warp_round(La, lane, as, ac);
-    if (lane == 0) {
         // the item values and the scale come from the setup kernel
         cudaGridDependencySynchronize();
-        const bool ovf = __ldcg(A.cta_done + 1) != 0u;
+        ovf = __ldcg(A.cta_done + 1) != 0u;
+        g = A.item_integral[0];
+        V = A.vars[0];
+        if (g >= 0) B = A.bases[g];
+        oi = A.items[0].out;
+    }
+    double s, c;
+    la_warp_round(L, lane, s, c);
+    if (two) {
+        if (threadIdx.x == 32) s_r[0] = s + c;
+        asm volatile("bar.sync 1, 64;" ::: "memory");  // the two rounding warps
+    } else {
+        double as, ac;
+        la_warp_round(La, lane, as, ac);
+        if (threadIdx.x == 0) s_r[0] = as + ac;
+    }
+    if (threadIdx.x == 0) {
         const double T = ovf ? __longlong_as_double(0x7ff8000000000000ll) : s + c;
-        assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, A.flags, A.guard_tol,
-                      A.unit_roundoff, 0, T, as + ac);
+        assemble_values(V, B, g, oi, A.out, A.vout, A.flags, A.guard_tol, A.unit_roundoff, 0, T, s_r[0]);
         *A.work = 0ull;
         A.cta_done[0] = 0u;
         A.cta_done[1] = 0u;
@@ -650,13 +674,14 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_la[2 * SG_LA_DIGITS];
     __shared__ int s_flag[2];
+    __shared__ double s_r[1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     PS *sP = (PS *)smem + (size_t)warp * SG_APAD;
     SgPrefixPos *sPos = (SgPrefixPos *)(smem + (size_t)nw * SG_APAD * sizeof(PS)) + warp * SG_MAX_R;
     int *sIdx = (int *)(smem + (size_t)nw * (SG_APAD * sizeof(PS) + SG_MAX_R * sizeof(SgPrefixPos))) + warp * SG_MAX_R;
     bool waited = false;
     if (A.single) {
-        if ((int)threadIdx.x < 2 * SG_LA_DIGITS) s_la[threadIdx.x] = 0;
+        for (int k = threadIdx.x; k < 2 * SG_LA_DIGITS; k += blockDim.x) s_la[k] = 0;
         if (threadIdx.x == 0) s_flag[0] = 0;
         __syncthreads();
     }
@@ -790,7 +815,7 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
         }
         complete_chunk(A, item, c, lane);
     }
-    if (A.single) finish_single(A, s_la, s_flag);
+    if (A.single) finish_single(A, s_la, s_flag, s_r);
 }
 
 // Float fold: register budget for 4 CTAs of 8 warps per SM.  Double fold:

@@ -810,7 +810,7 @@ extern "C" sg_status sg_shard_combine(const long long *const *partials, int nsha
         r.mant = mant;
         r.exp2 = (int64_t)(I.scale_e2 + e1);
         r.value = ldexp(mant, (int)(I.scale_e2 + e1));
-        r.cond = absrel / fabs(rel);
+        r.cond = sg_ratio(absrel, fabs(rel));
         r.err_est = 0.05 * I.unit_roundoff * r.cond;
         r.points = I.points;
         r.evals = I.evals;

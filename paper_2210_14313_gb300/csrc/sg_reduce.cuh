@@ -20,20 +20,18 @@ __device__ __forceinline__ void neu_add(double &s, double &c, double v) {
 
 // Value of a finished item: mult * (base_rel + T), relative to the
 // integral's scale exp(log f(c)).  Forward items write their output record
-// as Q = mant * 2^exp2; adjoint sub-sums write their relative value.
-__device__ inline void assemble_item(const SgItemDev *items, const SgItemVar *vars, const SgBaseDev *bases,
-                              const int *item_integral, SgOutDev *out, double *vout, int *flags,
-                              double guard_tol, double unit_roundoff, int item, double T, double AB) {
-    const SgItemDev *I = items + item;
-    const SgItemVar V = vars[item];
+// as Q = mant * 2^exp2; adjoint sub-sums write their relative value.  The
+// item's values V, the integral's base B (g < 0: an adjoint sub-sum) and
+// its output index come from the caller, which can load them early.
+__device__ inline void assemble_values(const SgItemVar &V, const SgBaseDev &B, int g, long long out_idx,
+                                       SgOutDev *out, double *vout, int *flags, double guard_tol,
+                                       double unit_roundoff, int item, double T, double AB) {
     const double rel = V.mult * (V.base_rel + T);
     const double absrel = fabs(V.mult) * (fabs(V.base_rel) + AB);
-    const int g = item_integral[item];
     if (g < 0) {
-        vout[I->out] = rel;
+        vout[out_idx] = rel;
         return;
     }
-    const SgBaseDev B = bases[g];
     // Q = exp(log_hi + log_lo) * rel = 2^e0 * scale_m * rel
     const double e0 = B.scale_e2;
     int e1 = 0;
@@ -42,12 +40,20 @@ __device__ inline void assemble_item(const SgItemDev *items, const SgItemVar *va
     o.mant = mant;
     o.exp2 = e0 + e1;
     o.value = ldexp(mant, (int)(e0 + e1));
-    o.cond = absrel / fabs(rel);
+    o.cond = sg_ratio(absrel, fabs(rel));  // three digits suffice for the error estimate
     o.err_est = 0.05 * unit_roundoff * o.cond;
     o.sum = rel;
     o.abs_sum = absrel;
-    out[I->out] = o;
+    out[out_idx] = o;
     if (flags && guard_tol > 0.0) flags[item] = o.err_est > guard_tol ? 1 : 0;
+}
+
+__device__ inline void assemble_item(const SgItemDev *items, const SgItemVar *vars, const SgBaseDev *bases,
+                              const int *item_integral, SgOutDev *out, double *vout, int *flags,
+                              double guard_tol, double unit_roundoff, int item, double T, double AB) {
+    const int g = item_integral[item];
+    const SgBaseDev B = g >= 0 ? bases[g] : SgBaseDev{};
+    assemble_values(vars[item], B, g, items[item].out, out, vout, flags, guard_tol, unit_roundoff, item, T, AB);
 }
 
 // Warp-wide exact sums (sg_xsum.h): the largest exponent among the lanes'

@@ -16,6 +16,7 @@
 #if defined(__CUDACC__) || defined(__CUDACC_RTC__)
 #define SG_XS __host__ __device__ __forceinline__
 #else
+#include <math.h>
 #include <string.h>
 #define SG_XS static inline
 #endif
@@ -52,6 +53,29 @@ SG_XS int sg_xs_clz(unsigned long long v) {
 #else
     return v ? __builtin_clzll(v) : 64;
 #endif
+}
+
+// a / b (a, b >= 0) to float precision without an FP64 division (on GB300
+// a chain of dependent FP64 steps): the quotient of the significands in
+// float, the exponents subtracted as integers.  Zeros, subnormals,
+// infinities and NaNs take the double division.  The kernels' output
+// records and the host's combine of sharded batches both form the
+// condition number with it, so that the two agree bit for bit.
+SG_XS double sg_ratio(double a, double b) {
+    const unsigned long long ba = sg_xs_bits(a), bb = sg_xs_bits(b);
+    const int ea = (int)((ba >> 52) & 0x7ff), eb = (int)((bb >> 52) & 0x7ff);
+    if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff) return a / b;
+    const unsigned int fa = 0x3f800000u | (unsigned int)((ba >> 29) & 0x7fffff);
+    const unsigned int fb = 0x3f800000u | (unsigned int)((bb >> 29) & 0x7fffff);
+#if defined(__CUDA_ARCH__)
+    const float q = __fdiv_rn(__uint_as_float(fa), __uint_as_float(fb));
+#else
+    float ma, mb;
+    memcpy(&ma, &fa, sizeof(ma));
+    memcpy(&mb, &fb, sizeof(mb));
+    const float q = ma / mb;
+#endif
+    return ldexp((double)q, ea - eb);
 }
 
 // biased exponent of |v| (1 for zero and subnormals)
