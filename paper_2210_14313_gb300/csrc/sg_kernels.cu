@@ -504,6 +504,18 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
             const int At = a_hi - ab < SG_APAD ? a_hi - ab : SG_APAD;
             // fold the prefix directions: one state per prefix node tuple (its
             // digits in the mixed radix of the block sizes, the last fastest)
+            // the table rows of every position are first requested into L1
+            // (prefetches carry no data, so they are all in flight at once and
+            // a prefix costs about one memory latency, not one per position)
+            for (int a = lane; a < At; a += 32) {
+                int q = ab + a;
+                for (int t = r - 2; t >= 0; t--) {
+                    const SgPrefixPos pp = sPos[t];
+                    const int qn = sg_div_magic_q(q, pp.dm);
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(tab + pp.row + (q - qn * pp.m)));
+                    q = qn;
+                }
+            }
             for (int a = lane; a < At; a += 32) {
                 int q = ab + a;
                 if constexpr (std::is_same<T, FFTag>::value) {  // float-float
@@ -584,7 +596,20 @@ __device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la,
     if (threadIdx.x == 0 && s_flag[0]) atomicOr(A.cta_done + 1, 1u);
     __threadfence();  // this CTA's additions before its count (one fence serves both)
     __syncthreads();
-    if (threadIdx.x == 0) s_flag[1] = atomicAdd(A.cta_done, 1u) == gridDim.x - 1;
+    // the values the assembly needs (from the setup kernel; one item, integral
+    // 0), requested by every CTA's thread 0 together with its count, so that
+    // the last CTA has them when its sums are rounded
+    SgItemVar V;
+    SgBaseDev B;
+    long long oi = 0;
+    const int g = 0;
+    if (threadIdx.x == 0) {
+        cudaGridDependencySynchronize();
+        V = A.vars[0];
+        B = A.bases[0];
+        oi = A.items[0].out;
+        s_flag[1] = atomicAdd(A.cta_done, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     // two warps: warp 0 holds the sum's limbs, warp 1 the absolute sum's (a
     // one-warp CTA rounds both in turn)
@@ -599,20 +624,8 @@ __device__ __noinline__ void finish_single(const SgFoldArgs &A, long long *s_la,
         La = __ldcg(A.lacc + SG_LA_DIGITS + lane);
         A.lacc[SG_LA_DIGITS + lane] = 0;
     }
-    SgItemVar V;
-    SgBaseDev B;
-    int g = 0;
-    long long oi = 0;
     bool ovf = false;
-    if (threadIdx.x == 0) {
-        // the item values and the scale come from the setup kernel
-        cudaGridDependencySynchronize();
-        ovf = __ldcg(A.cta_done + 1) != 0u;
-        g = A.item_integral[0];
-        V = A.vars[0];
-        if (g >= 0) B = A.bases[g];
-        oi = A.items[0].out;
-    }
+    if (threadIdx.x == 0) ovf = __ldcg(A.cta_done + 1) != 0u;
     double s, c;
     la_warp_round(L, lane, s, c);
     if (two) {
@@ -893,63 +906,74 @@ __global__ void __launch_bounds__(256) sg_setup_kernel(SgSetupArgs A, int nbase)
         // threads' sums to the largest unit and adds them as integers.  The
         // result is the same on every call, and no FP64 operation sits in a
         // dependency chain (on GB300 each would cost ~10^2 cycles).
+        // Up to 32 terms take one warp and no block barriers (every step
+        // here is latency on the path of a single integral; longer sums are
+        // faster spread over the block).
+        const bool one_warp = G.d <= 32;
+        if (one_warp && warp > 0 && !(A.do_items && ti1 - ti0 > 1)) return;
         SgX acc = {0ull, 0ull};
         int E = 1;
-        if (G.fam != SG_FAM_USER)  // a user integrand's parameters have no fixed layout
-            for (int i = threadIdx.x; i < G.d; i += blockDim.x)
+        if (G.fam != SG_FAM_USER && (!one_warp || warp == 0))  // a user integrand's parameters have no fixed layout
+            for (int i = one_warp ? lane : (int)threadIdx.x; i < G.d; i += one_warp ? 32 : (int)blockDim.x)
                 sg_x_add_adaptive(acc, E, phi_centre(G.fam, a[i], u[i]));
-        const int Ew = warp_max_exp(E);
-        if (lane == 0) sh_e[warp] = Ew;
-        __syncthreads();
-        int Eb = sh_e[0];
-        for (int w = 1; w < nw; w++) Eb = max(Eb, sh_e[w]);
-        sg_x_shr(acc, Eb - E);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            SgX b;
-            b.lo = __shfl_xor_sync(FULL_MASK, acc.lo, o);
-            b.hi = __shfl_xor_sync(FULL_MASK, acc.hi, o);
-            sg_x_plus(acc, b);
+        int Eb = warp_max_exp(E);
+        if (!one_warp) {
+            if (lane == 0) sh_e[warp] = Eb;
+            __syncthreads();
+            Eb = sh_e[0];
+            for (int w = 1; w < nw; w++) Eb = max(Eb, sh_e[w]);
         }
-        if (lane == 0) sh_x[warp] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            if (lane == 0) {
-                SgX t = sh_x[0];
+        sg_x_shr(acc, Eb - E);
+        warp_xadd(acc);
+        if (!one_warp) {
+            if (lane == 0) sh_x[warp] = acc;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            SgX t = acc;
+            if (!one_warp) {
+                t = sh_x[0];
                 for (int w = 1; w < nw; w++) sg_x_plus(t, sh_x[w]);
-                double s, c;
-                sg_x_pair(t, Eb, &s, &c);
-                SgBaseDev B;
-                if (G.fam == 1) {
-                    B.log_hi = 0.0;
-                    B.log_lo = 0.0;
-                    sg_sincos_d(6.28318530717958647693 * u[0] + (s + c), &B.sin_th, &B.cos_th);
-                    B.base = B.cos_th;
-                } else {
-                    B.log_hi = s;
-                    B.log_lo = c;
-                    B.base = 1.0;
-                    B.sin_th = 0.0;
-                    B.cos_th = 1.0;
-                }
-                // exp(log_hi + log_lo) = 2^e0 exp(r), r = log_hi - e0 ln 2 + log_lo with
-                // ln 2 split in two (Cody & Waite): the result's scale without overflow
-                // (1 for the oscillatory family, whose values are not scaled)
-                if (B.log_hi == 0.0 && B.log_lo == 0.0) {
-                    B.scale_e2 = 0.0;
-                    B.scale_m = 1.0;
-                } else {
-                    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-                    const double e0 = floor(B.log_hi * 1.44269504088896338700);
-                    const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
-                    B.scale_e2 = e0;
-                    B.scale_m = 1.0 + sg_expm1_d(rr);
-                }
-                A.bases[g] = B;
-                sh_b = B;
+            }
+            double s, c;
+            sg_x_pair(t, Eb, &s, &c);
+            SgBaseDev B;
+            if (G.fam == 1) {
+                B.log_hi = 0.0;
+                B.log_lo = 0.0;
+                sg_sincos_d(6.28318530717958647693 * u[0] + (s + c), &B.sin_th, &B.cos_th);
+                B.base = B.cos_th;
+            } else {
+                B.log_hi = s;
+                B.log_lo = c;
+                B.base = 1.0;
+                B.sin_th = 0.0;
+                B.cos_th = 1.0;
+            }
+            // exp(log_hi + log_lo) = 2^e0 exp(r), r = log_hi - e0 ln 2 + log_lo with
+            // ln 2 split in two (Cody & Waite): the result's scale without overflow
+            // (1 for the oscillatory family, whose values are not scaled)
+            if (B.log_hi == 0.0 && B.log_lo == 0.0) {
+                B.scale_e2 = 0.0;
+                B.scale_m = 1.0;
+            } else {
+                const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+                const double e0 = floor(B.log_hi * 1.44269504088896338700);
+                const double rr = ((B.log_hi - e0 * ln2_hi) - e0 * ln2_lo) + B.log_lo;
+                B.scale_e2 = e0;
+                B.scale_m = 1.0 + sg_expm1_d(rr);
+            }
+            A.bases[g] = B;
+            sh_b = B;
+            if (A.do_items && ti1 - ti0 == 1) {
+                // one item (a single forward integral): its values right away
+                A.vars[it0] = item_values(role0, G, B, A.params);
+                if (nch0 == 0)
+                    assemble_item(A.items, A.vars, A.bases, A.item_integral, A.out, A.vout, nullptr, 0.0,
+                                  A.unit_roundoff, it0, 0.0, 0.0);
             }
         }
-        if (!A.do_items) return;
+        if (!A.do_items || ti1 - ti0 == 1) return;
         __syncthreads();
         const SgBaseDev B = sh_b;
         for (int t = ti0 + threadIdx.x; t < ti1; t += blockDim.x) {

@@ -311,16 +311,23 @@ bool count_points(int kind, int d, int L, u64 *out) {
 // prefix block), and runs are cut between subsets where needed.
 
 // Lane slots of k subsets of one run of a pattern with A prefix tuples and
-// tm tail nodes (k * tm tail entries per prefix tuple).
-static u64 run_slots(u64 A, u64 tm, u64 k) {
-    const u64 kPrefixSlots = 16;  // a prefix fold: about half a pass
+// tm tail nodes (k * tm tail entries per prefix tuple), with `run` slots for
+// the fixed work of a run and prefix block (its prefix fold and the loads
+// of new table rows, a few memory latencies whatever the points).
+static u64 run_slots(u64 A, u64 tm, u64 k, u64 run) {
     u64 c = 0;
     for (u64 b = 0; b * SG_APAD < A; b++) {
         const u64 At = std::min<u64>(SG_APAD, A - b * SG_APAD);
-        c += 32 * ((At * k * tm + 31) / 32) + kPrefixSlots;
+        c += 32 * ((At * k * tm + 31) / 32) + run;
     }
     return c;
 }
+
+// The fixed work of a run in lane slots, by precision: measured on GB300 as
+// about 0.3 of an FP64 pass (1.1 - 1.6 us per pass of 32 points), 3 - 4
+// float passes (0.4 - 0.5 us each) and 2 float-float passes; the latency of
+// a run is the same, the passes it is set against differ.
+static u64 run_cost_slots(int prec) { return prec == 0 ? 24 : (prec == 1 ? 112 : 64); }
 
 // Calls fn(len) for the runs of the r-subsets of d directions in the
 // fold's order: prefix tuples p_0 < .. < p_{r-2} <= d - 2 in lexicographic
@@ -346,7 +353,7 @@ template <class F> static void for_each_run(int d, int r, F fn) {
 // its lane slots would pass `budget`; consecutive chunks of equal size share
 // one record (the last chunk of a record may be smaller).  With P null the
 // chunks are only counted.  Returns the number of chunks.
-static u64 chunk_by_runs(const SgPatDev &pd, int d, u64 budget, u64 &chunk, Plan *P) {
+static u64 chunk_by_runs(const SgPatDev &pd, int d, u64 budget, u64 run, u64 &chunk, Plan *P) {
     const u64 A = (u64)pd.A, tm = (u64)pd.tm;
     std::vector<u64> sizes;  // subsets per chunk
     u64 cur = 0, cur_n = 0;
@@ -357,8 +364,8 @@ static u64 chunk_by_runs(const SgPatDev &pd, int d, u64 budget, u64 &chunk, Plan
     };
     for_each_run(d, pd.r, [&](u64 m) {
         while (m > 0) {
-            if (cur + run_slots(A, tm, m) <= budget) {
-                cur += run_slots(A, tm, m);
+            if (cur + run_slots(A, tm, m, run) <= budget) {
+                cur += run_slots(A, tm, m, run);
                 cur_n += m;
                 return;
             }
@@ -366,12 +373,12 @@ static u64 chunk_by_runs(const SgPatDev &pd, int d, u64 budget, u64 &chunk, Plan
             u64 lo = 0, hi = m;
             while (lo < hi) {
                 const u64 mid = (lo + hi + 1) / 2;
-                if (cur + run_slots(A, tm, mid) <= budget) lo = mid;
+                if (cur + run_slots(A, tm, mid, run) <= budget) lo = mid;
                 else hi = mid - 1;
             }
             if (lo == 0 && cur_n == 0) lo = 1;
             if (lo > 0) {
-                cur += run_slots(A, tm, lo);
+                cur += run_slots(A, tm, lo, run);
                 cur_n += lo;
                 m -= lo;
             }
@@ -587,6 +594,7 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
     for (const Req &R : reqs) by_runs = by_runs && R.ppc == 0;
     std::vector<std::vector<char>> use_runs(ib.size());
     u64 slot_budget = 0;
+    const u64 rc = run_cost_slots(prec);
     if (by_runs) {
         unsigned __int128 run_budget = (unsigned __int128)1 << 22;
         u64 slots = 0;
@@ -611,7 +619,7 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
                 if (runs <= run_budget) {
                     run_budget -= runs;
                     use_runs[order[q]][k] = 1;
-                    for_each_run(b.it.d, sp.r, [&](u64 m) { slots += run_slots((u64)pd.A, (u64)pd.tm, m); });
+                    for_each_run(b.it.d, sp.r, [&](u64 m) { slots += run_slots((u64)pd.A, (u64)pd.tm, m, rc); });
                 } else {
                     slots += nsub * (u64)pd.A * (u64)pd.tm;
                 }
@@ -627,14 +635,14 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
                     if (!use_runs[order[q]][k]) continue;
                     SgPatDev pd;
                     pattern_shape(b, b.specs[k], pd);
-                    if (run_slots((u64)pd.A, (u64)pd.tm, 1) > budget) return ~0ull;
+                    if (run_slots((u64)pd.A, (u64)pd.tm, 1, rc) > budget) return ~0ull;
                     u64 none = 0;
-                    n += chunk_by_runs(pd, b.it.d, budget, none, nullptr);
+                    n += chunk_by_runs(pd, b.it.d, budget, rc, none, nullptr);
                 }
             }
             return n;
         };
-        u64 lo = std::max<u64>(slots / warps + 1, 48), hi = lo;
+        u64 lo = std::max<u64>(slots / warps + 1, 32 + rc), hi = lo;
         while (count(hi) > warps && hi < (1ull << 40)) hi *= 2;
         while (lo < hi) {  // the count does not grow with the budget
             const u64 mid = lo + (hi - lo) / 2;
@@ -699,8 +707,8 @@ sg_status build_plan_host(const std::vector<Req> &reqs, int prec, const sg_tunin
                 P->pat_chunk0.push_back(rec.chunk0);
             };
             const u64 pe = nsub * per_sub;
-            if (by_runs && use_runs[order[q]][ks] && run_slots(A, (u64)pd.tm, 1) <= slot_budget) {
-                chunk_by_runs(pd, b.it.d, slot_budget, chunk, P);
+            if (by_runs && use_runs[order[q]][ks] && run_slots(A, (u64)pd.tm, 1, rc) <= slot_budget) {
+                chunk_by_runs(pd, b.it.d, slot_budget, rc, chunk, P);
                 done += pe;
                 continue;
             }
