@@ -385,9 +385,16 @@ static sg_status get_plan(const std::vector<Req> &reqs, int prec, Plan **out) {
         *out = it->second;
         return SG_OK;
     }
+    // FP64 folds come in two builds (sg_kernels.cu): a single integral, which
+    // is latency-bound, takes the one without a register budget (2 CTAs per
+    // SM); batches take the one for 3 CTAs per SM
+    const bool narrow = prec == SG_PREC_FP64 && reqs.size() == 1 && reqs[0].ppc == 0;
+    sg_tuning t = k.t;
+    if (narrow) t.ctas_per_sm = std::min(t.ctas_per_sm, 2);
     Plan *P = nullptr;
-    st = build_plan(reqs, prec, k.t, resident_warps(C, prec, k.t), C->binom, &P);
+    st = build_plan(reqs, prec, t, resident_warps(C, prec == SG_PREC_FP64 && !narrow ? 3 : prec, t), C->binom, &P);
     if (st != SG_OK) return st;
+    P->narrow = narrow;
     if (g_plans.size() > 256) {  // bound the cache
         cudaDeviceSynchronize();
         drop_all_graphs();
@@ -581,7 +588,11 @@ static sg_status ws_prepare(Workspace *W, const Plan *P, bool need32, bool need6
     return SG_OK;
 }
 
+// The fold build for a plan and precision (sg_launch_fold's prec code).
+static int fold_kind(const Plan *P, int prec) { return prec == SG_PREC_FP64 && !P->narrow ? 3 : prec; }
+
 static SgLaunchCfg fold_cfg(const Plan *P, int prec, DevCtx *C) {
+    prec = fold_kind(P, prec);
     SgLaunchCfg c;
     c.warps_per_cta = P->tune.warps_per_cta;
     int occ = dev_occupancy(C, prec, c.warps_per_cta);
@@ -733,7 +744,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
     if (items_lacc) CK(cudaMemsetAsync(W->ilacc.p, 0, ilacc_bytes, s));
     CK(prof_mark(W, true, s));
     if (uf) CK(launch_user_fold(*uf, fa, P, C, s));
-    else CK(sg_launch_fold(fa, prec, 0, fold_cfg(P, prec, C), s));
+    else CK(sg_launch_fold(fa, fold_kind(P, prec), 0, fold_cfg(P, prec, C), s));
     CK(prof_mark(W, false, s));
     if (single) W->la_clean = true;
     if (prec == 1 && guard_tol > 0.0) {
@@ -765,7 +776,7 @@ static sg_status run_plan(const Plan *P, Workspace *W, DevCtx *C, const double *
         fa.guard_tol = 0.0;
         fa.unit_roundoff = unit_roundoff(0);
         CK(prof_mark(W, true, s));
-        CK(sg_launch_fold(fa, 0, 0, fold_cfg(P, 0, C), s));
+        CK(sg_launch_fold(fa, fold_kind(P, 0), 0, fold_cfg(P, 0, C), s));
         CK(prof_mark(W, false, s));
     }
     // leave the counters of the single-integral fold as it expects them

@@ -504,16 +504,24 @@ __device__ void fold_chunk(const SgFoldArgs &A, const SgPatDev *__restrict__ P,
             const int At = a_hi - ab < SG_APAD ? a_hi - ab : SG_APAD;
             // fold the prefix directions: one state per prefix node tuple (its
             // digits in the mixed radix of the block sizes, the last fastest)
-            // the table rows of every position are first requested into L1
-            // (prefetches carry no data, so they are all in flight at once and
-            // a prefix costs about one memory latency, not one per position)
-            for (int a = lane; a < At; a += 32) {
-                int q = ab + a;
-                for (int t = r - 2; t >= 0; t--) {
-                    const SgPrefixPos pp = sPos[t];
-                    const int qn = sg_div_magic_q(q, pp.dm);
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(tab + pp.row + (q - qn * pp.m)));
-                    q = qn;
+            // FP64, d > 32: the table rows of every position are first
+            // requested into L1 (prefetches carry no data, so they are all in
+            // flight at once).  Large tables are read mostly once per SM, and
+            // one latency per prefix instead of one per position took a
+            // d = 100 integral from 45 to 38 us; small tables stay in L1 and
+            // float folds are issue-bound, and there the extra pass costs
+            // (d = 12: 25 -> 29 us; a float batch: +10%).
+            if constexpr (std::is_same<T, double>::value) {
+                if (d > 32) {
+                    for (int a = lane; a < At; a += 32) {
+                        int q = ab + a;
+                        for (int t = r - 2; t >= 0; t--) {
+                            const SgPrefixPos pp = sPos[t];
+                            const int qn = sg_div_magic_q(q, pp.dm);
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(tab + pp.row + (q - qn * pp.m)));
+                            q = qn;
+                        }
+                    }
                 }
             }
             for (int a = lane; a < At; a += 32) {
@@ -831,10 +839,16 @@ __device__ __forceinline__ void fold_kernel_body(const SgFoldArgs &A) {
     if (A.single) finish_single(A, s_la, s_flag, s_r);
 }
 
-// Float fold: register budget for 4 CTAs of 8 warps per SM.  Double fold:
-// no occupancy constraint (a few warps already saturate GB300's FP64 pipe).
+// Float fold: register budget for 4 CTAs of 8 warps per SM.  Double fold,
+// two builds: without a register budget (84 registers, 2 CTAs of 8 warps
+// per SM) for single integrals, and with one for 3 CTAs per SM (80
+// registers, a few bytes spilled) for batches, whose throughput gains 10 -
+// 13% from the extra warps covering the dependent integer chains of the
+// fixed-point deviation; on single integrals of d = 100 and 1000 the spill
+// cost 25% (measured on GB300).
 __global__ void __launch_bounds__(256, 4) sg_fold_kernel_f(SgFoldArgs A) { fold_kernel_body<float>(A); }
 __global__ void sg_fold_kernel_d(SgFoldArgs A) { fold_kernel_body<double>(A); }
+__global__ void __launch_bounds__(256, 3) sg_fold_kernel_d3(SgFoldArgs A) { fold_kernel_body<double>(A); }
 __global__ void __launch_bounds__(256, 2) sg_fold_kernel_x(SgFoldArgs A) { fold_kernel_body<FFTag>(A); }
 
 // ---------------------------------------------------------------------------
@@ -1152,6 +1166,8 @@ cudaError_t sg_launch_setup(const SgSetupArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// prec: 0 FP64 (single-integral build), 1 float, 2 float-float, 3 FP64
+// (batch build, 3 CTAs per SM)
 static size_t fold_smem(int prec, int warps) {
     const size_t psz = prec == 1 ? sizeof(float2) : (prec == 2 ? sizeof(float4) : sizeof(double2));
     return (size_t)warps * (SG_APAD * psz + SG_MAX_R * (sizeof(SgPrefixPos) + sizeof(int)));
@@ -1165,6 +1181,8 @@ int sg_fold_occupancy(int prec, int gk, int warps_per_cta) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_x, 32 * warps_per_cta, sm);
     else if (prec == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_f, 32 * warps_per_cta, sm);
+    else if (prec == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_d3, 32 * warps_per_cta, sm);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sg_fold_kernel_d, 32 * warps_per_cta, sm);
     return n;
@@ -1188,6 +1206,7 @@ cudaError_t sg_launch_fold(const SgFoldArgs &a, int prec, int gk, SgLaunchCfg cf
     lc.numAttrs = cfg.dependent ? 1 : 0;
     if (prec == 2) return cudaLaunchKernelEx(&lc, sg_fold_kernel_x, a);
     if (prec == 1) return cudaLaunchKernelEx(&lc, sg_fold_kernel_f, a);
+    if (prec == 3) return cudaLaunchKernelEx(&lc, sg_fold_kernel_d3, a);
     return cudaLaunchKernelEx(&lc, sg_fold_kernel_d, a);
 }
 

@@ -47,6 +47,7 @@ struct Req {
 
 struct Plan {
     unsigned long long id = 0;  // unique per built plan (never reused, unlike its address)
+    bool narrow = false;        // a single FP64 integral: the fold build for 2 CTAs per SM
     std::vector<Req> reqs;
     int prec = 0;
     sg_tuning tune{};
