@@ -11,6 +11,9 @@ default, each with its own seeded parameter draw), each a full single-integral
 call (table setup, item values, the persistent fold kernel and the
 deterministic reduction), issued back to back on one stream.  The metric's
 unit is n_d^q, the point count of Eq. 2.6 with repetition (593,775 here).
+The configurations under "extra" are timed the same way (64 draws back to
+back, inputs resident on the device), each beside the latency of one
+blocking call with host parameters on an idle GPU ("s_isolated_call").
 
 --impl reference times the CPU oracle (the plain enumeration the tests use
 as ground truth) on the host cores instead.
@@ -36,7 +39,7 @@ METRIC = "effective sparse-grid points/sec and s/integral at stated rel. error v
 # summarised in profiles/sg_fold_kernel_d__cfg2_d12_gl_L6_oscillatory.txt.
 # Valid only for the kernel sources with this digest; otherwise reported as
 # null until the capture is taken again.
-_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (331264, "91ca25a99c0d30b0")}
+_FOLD_TRAFFIC = {"cfg2_d12_gl_L6_oscillatory": (396544, "5a40fb25d655a1e7")}
 _KERNEL_SOURCES = ["paper_2210_14313_gb300/csrc/sg_kernels.cu", "paper_2210_14313_gb300/csrc/sg_fold_logic.h",
                    "paper_2210_14313_gb300/csrc/sg_ff.cuh", "paper_2210_14313_gb300/csrc/sg_internal.h",
                    "paper_2210_14313_gb300/csrc/sg_reduce.cuh", "paper_2210_14313_gb300/csrc/sg_fixed.h",
@@ -410,6 +413,7 @@ def _extras(sg, oracle, torch, args):
     """The other configurations on one GPU: the precision ladder with the
     fold's roofline, the gradient of the d = 1000 configuration, the batched
     form of the headline workload, and a subset of the 4096-item batch."""
+    import ctypes
     import numpy as np
     import sg_inputs as si
     rules = {k: sg.Rule(k, max_level=8) for k in (2, 4)}
@@ -420,18 +424,42 @@ def _extras(sg, oracle, torch, args):
         ref = oracle.integrate(c["rule"], c["fam"], c["params"], c["d"], c["L"])
         rule = rules[c["rule"]]
         row = {"points": oracle.count_points(c["rule"], c["d"], c["L"])}
+        # R draws resident on the device, integrated back to back through the
+        # asynchronous entry point (as the headline step), events around them;
+        # and the latency of one blocking call with host parameters, GPU idle
+        R = 64
+        dpar = torch.tensor(np.stack([si.redraw(c, j) for j in range(R)]), dtype=torch.float64, device="cuda")
+        dout = torch.zeros((R, sg.DEV_RESULT_DOUBLES), dtype=torch.float64, device="cuda")
+        q = c["d"] + c["L"]
+        lib = sg.load()
+        sh = ctypes.c_void_p(stream.cuda_stream)
         for prec in (0, 1, 2):
+            calls = [(rule.handle, c["fam"], ctypes.c_void_p(dpar[j].data_ptr()), c["d"], q, prec, sg.FORM_AUTO,
+                      sh, ctypes.c_void_p(dout[j].data_ptr())) for j in range(R)]
+
+            def run():
+                for a in calls:
+                    if lib.sg_integrate_async(*a) != 0:
+                        raise RuntimeError("sg_integrate_async failed")
             for _ in range(3):
-                sg.integrate(rule, c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec)
-            ts = []
+                run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
             sg.profile_begin(stream)
-            for _ in range(21):
-                r = sg.integrate(rule, c["fam"], c["params"], c["d"], c["d"] + c["L"], prec=prec)
-                ts.append(r.seconds)
+            run()
             fold_ms, nl = sg.profile_end(stream)
-            t = sorted(ts)[10]
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3 / R
+            ts = []
+            for _ in range(11):
+                r = sg.integrate(rule, c["fam"], c["params"], c["d"], q, prec=prec)
+                ts.append(r.seconds)
             rr = _fold_roofline(sg, prec, 1 if c["fam"] == 1 else 0, r.points, r.evals, fold_ms, nl)
             row[names[prec]] = {"s_per_integral": t, "points_per_s": row["points"] / t, "rel_err": _rel(r, ref),
+                                "s_isolated_call": sorted(ts)[5],
                                 "err_est": r.err_est, "evals": r.evals,
                                 "roofline": {k: rr[k] for k in ("achieved", "peak", "frac", "frac_evals",
                                                                 "fold_us")}}
