@@ -35,7 +35,7 @@ def _load():
 
 def run(kind, fam, params, d, L, form=2, grad=0, ppc=2048, ctas_per_sm=8, warps=8):
     p = np.ascontiguousarray(params, dtype=np.float64)
-    out = np.zeros(9)
+    out = np.zeros(10)
     nv = ctypes.c_longlong(0)
     cap = 2 * d * 64 if grad else 1
     v = np.zeros(max(cap, 1))
@@ -47,6 +47,7 @@ def run(kind, fam, params, d, L, form=2, grad=0, ppc=2048, ctas_per_sm=8, warps=
         raise RuntimeError("chk_run failed with %d" % rc)
     return dict(rel=out[0], logscale=out[1], violations=int(out[2]), badpairs=int(out[3]),
                 evals=int(out[4]), chunks=int(out[5]), plan_evals=int(out[6]), rel_shift=out[7], lane_slots=int(out[8]),
+                max_runs=int(out[9]),
                 v=v[:nv.value])
 
 

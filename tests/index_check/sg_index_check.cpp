@@ -70,7 +70,8 @@ extern "C" {
 // (i.e. base + T times the multiplier), out[1] = log f(c) (exponential
 // families), out[2] = number of bound violations, out[3] = pairs visited
 // other than exactly once, out[4] = evaluations, out[5] = chunks,
-// out[6] = evaluations the plan claims, out[8] = lane slots of the point
+// out[6] = evaluations the plan claims, out[9] = the most runs (subsets
+// sharing a prefix) in one chunk, out[8] = lane slots of the point
 // loop (32 x warp passes; evaluations / slots is the lane occupancy).  vout receives the adjoint sub-sums
 // (nv entries, may be NULL); nv_out their count.
 int chk_run(int kind, int fam, const double *params, int d, int L, int form, int grad, int ppc,
@@ -150,7 +151,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
 
     long long violations = 0, badpairs = 0;
     unsigned long long evals = 0;
-    long long lane_slots = 0;
+    long long lane_slots = 0, max_runs = 0;
     std::vector<double> slot(P->nchunks, 0.0);
     int idx[SG_MAX_R];
     for (unsigned long long c = 0; c < P->nchunks; c++) {
@@ -208,7 +209,9 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
             return true;
         };
         double acc = 0.0;
+        long long runs = 0;
         while (cnt > 0) {
+            runs++;
             const int plast = idx[r - 1];
             const int run = (unsigned long long)(dd - plast) < cnt ? dd - plast : (int)cnt;
             const SgTailSegs seg = sg_tail_segments(Pp->toff, Pp->tm, plast, run, skip);
@@ -280,6 +283,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
             if (cnt > 0 && !sg_next_prefix(idx, dd, r)) violations++;
         }
         slot[c] = acc * Pp->coef;
+        if (runs > max_runs) max_runs = runs;
     }
     // per-item fixed-order reduction and assembly
     std::vector<double> vals(P->nout, 0.0);
@@ -304,6 +308,7 @@ int chk_run(int kind, int fam, const double *params, int d, int L, int form, int
     out[6] = (double)P->total_evals;
     if (P->nout > 1) out[7] = vals[1];
     out[8] = (double)lane_slots;
+    out[9] = (double)max_runs;
     if (nv_out) *nv_out = nv;
     plan_free_host(P);
     return 0;

@@ -107,6 +107,26 @@ def test_chunking_does_not_change_the_sum(ppc, ctas, warps):
     assert _oracle_rel(c, r) < 1e-12
 
 
+@pytest.mark.parametrize("cfg,prec_ctas", [("cfg2", (2, 8)), ("cfg3", (2, 8)), ("cfg5", (2, 8)), ("cfg1", (2, 8))])
+def test_single_integral_chunks_are_one_wave_with_few_runs(cfg, prec_ctas):
+    # single integrals: the run-aware planner cuts the chunks by lane slots to
+    # no more than the resident warps (152 SMs x CTAs x warps), every pair
+    # still visited once; on d = 12 no chunk gathers the dozen short runs that
+    # points-only chunks did (at most a handful)
+    c = {"cfg1": si.cfg1, "cfg2": si.cfg2, "cfg5": si.cfg5}.get(cfg, lambda: si.cfg3(si.FAM_GAUSSIAN))()
+    ctas, warps = prec_ctas
+    r = index_check.run(c["rule"], c["fam"], c["params"], c["d"], c["L"], form=4, ppc=2048,
+                        ctas_per_sm=ctas, warps=warps)
+    assert r["violations"] == 0 and r["badpairs"] == 0
+    assert r["evals"] == r["plan_evals"]
+    assert r["chunks"] <= 152 * ctas * warps
+    if cfg == "cfg2":
+        assert r["max_runs"] <= 6
+    # (the replay adds each lane's terms in plain double, not exactly as the
+    # kernels do: merged weights of both signs cost it a few digits)
+    assert _oracle_rel(c, r) < 1e-11
+
+
 def test_merged_form_evaluates_each_distinct_point_once():
     # nested rules: the merged form's evaluations are the sparse grid's
     # distinct points less the centre (the oracle counts them by merging)
