@@ -222,7 +222,8 @@ def run_batch(args):
     batch in one persistent launch per precision tier (float evaluation; the
     items whose estimate exceeds 1e-6 / 4 again in float-float; what that
     still leaves above it in FP64), checked item by item against the separable
-    pin.  Minutes per step: not part of the default run."""
+    pin.  Minutes per step (by default one timed step after one warm-up step):
+    not part of the default run."""
     import numpy as np
     import torch
     import paper_2210_14313_gb300 as sg
@@ -626,8 +627,10 @@ def run_sweep(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    # defaults: 20 timed steps after 3 warm-up steps; the 4096-item batch
+    # (--workload cfg4, about 200 s per step) one step after one warm-up step
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--per-step", type=int, default=1024, help="integrals per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2")
@@ -638,6 +641,11 @@ def main():
                     help="run the complexity sweep of Section 6 instead of the benchmark")
     ap.add_argument("--sweep-budget", default="4e9", help="largest FP64 evaluation count per run")
     args = ap.parse_args()
+    batch = args.workload == "cfg4" and args.impl != "reference"
+    if args.steps is None:
+        args.steps = 1 if batch else 20
+    if args.warmup is None:
+        args.warmup = 1 if batch else 3
     if args.sweep:
         run_sweep(args)
         return
