@@ -127,6 +127,27 @@ def test_single_integral_chunks_are_one_wave_with_few_runs(cfg, prec_ctas):
     assert _oracle_rel(c, r) < 1e-11
 
 
+@pytest.mark.parametrize("case", [c for c in CASES if c["d"] >= 2 and c["rule"] & 16 == 0][:8],
+                         ids=lambda c: c["name"])
+def test_gradient_plan_enumeration(case):
+    # gradient plans (the forward item plus the adjoint sub-sums, which leave
+    # one direction out): with the run-aware chunks of single integrals every
+    # table access stays in its block and every pair is visited once
+    r = index_check.run(case["rule"], case["fam"], case["params"], case["d"], case["L"], form=2, grad=1)
+    assert r["violations"] == 0
+    assert r["badpairs"] == 0
+    assert r["evals"] == r["plan_evals"]
+    assert len(r["v"]) > 0 and np.all(np.isfinite(r["v"]))
+    assert _oracle_rel(case, r) < 1e-12
+    # the same sub-sums from point-sized chunks (one CTA of one warp per SM:
+    # chunk targets above the tuned maximum, so no run-aware chunking)
+    u = index_check.run(case["rule"], case["fam"], case["params"], case["d"], case["L"], form=2, grad=1,
+                        ppc=64, ctas_per_sm=1, warps=1)
+    assert u["violations"] == 0 and u["badpairs"] == 0
+    scale = max(1e-300, float(np.max(np.abs(r["v"]))))
+    assert np.max(np.abs(u["v"] - r["v"])) <= 1e-13 * scale
+
+
 def test_merged_form_evaluates_each_distinct_point_once():
     # nested rules: the merged form's evaluations are the sparse grid's
     # distinct points less the centre (the oracle counts them by merging)
