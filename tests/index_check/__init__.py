@@ -162,6 +162,18 @@ def lacc_x(v, nparts=1):
     return out[0], out[1], int(out[2]), out[3]
 
 
+def ratio(a, b):
+    """sg_ratio(a, b) elementwise (the library's float-precision quotient)."""
+    lib = _load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.chk_ratio.argtypes = [dp, dp, ctypes.c_longlong, dp]
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros(len(a))
+    lib.chk_ratio(a.ctypes.data_as(dp), b.ctypes.data_as(dp), len(a), out.ctypes.data_as(dp))
+    return out
+
+
 def merged_points(kind, d, L):
     """Every point of the merged form (distinct points of the sparse grid
     except the centre) with the planner's merged weight: (X[n, d], W[n])."""

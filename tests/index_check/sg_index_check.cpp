@@ -553,4 +553,10 @@ void chk_lacc_x(const double *v, long long n, int nparts, double *out) {
     out[2] = ovf;
 }
 
+// sg_ratio (the condition number's quotient without an FP64 division) over
+// n pairs.
+void chk_ratio(const double *a, const double *b, long long n, double *out) {
+    for (long long i = 0; i < n; i++) out[i] = sg_ratio(a[i], b[i]);
+}
+
 }  // extern "C"

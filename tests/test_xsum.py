@@ -143,3 +143,24 @@ def test_exact_window_digits_window_ends():
     assert index_check.lacc_x(np.array([1.0, float("inf")]), 1)[2] == 1
     assert index_check.lacc_x(np.array([1.0, float("nan")]), 2)[2] == 1
     assert index_check.lacc_x(np.array([0.0, -0.0]), 1)[:3] == (0.0, 0.0, 0)
+
+
+def test_ratio_to_float_precision():
+    # the condition number's quotient: within float rounding of the exact
+    # quotient for normal operands over the whole exponent range, the double
+    # division for zeros, subnormals, infinities and NaNs
+    rng = np.random.default_rng(4)
+    a = rng.uniform(0.5, 1, 20000) * 2.0 ** rng.integers(-500, 500, 20000)  # quotients stay normal
+    b = rng.uniform(0.5, 1, 20000) * 2.0 ** rng.integers(-500, 500, 20000)
+    q = index_check.ratio(a, b)
+    exact = [Fraction(x) / Fraction(y) for x, y in zip(a[:2000], b[:2000])]
+    for qi, e in zip(q[:2000], exact):
+        assert abs(Fraction(qi) - e) <= e * Fraction(2) ** -22
+    ref = a / b
+    ok = np.isfinite(ref) & (ref > 0)
+    assert np.all(np.abs(q[ok] - ref[ok]) <= 2.0 ** -22 * ref[ok])
+    special = index_check.ratio(np.array([0.0, 1.0, 5e-324, 1.0, np.inf, 1.0, 3.0]),
+                                np.array([1.0, 0.0, 1.0, 5e-324, 1.0, np.nan, 3.0]))
+    assert special[0] == 0.0 and special[1] == np.inf and special[2] == 5e-324
+    assert special[3] == 1.0 / 5e-324 and special[4] == np.inf and np.isnan(special[5])
+    assert special[6] == 1.0
