@@ -300,3 +300,24 @@ def test_class_tuning_table_loads_without_gpu(tmp_path):
     assert lib.sg_tuning_load(str(bad).encode(), ctypes.byref(n)) == 1          # bad precision
     assert lib.sg_tuning_load(str(tmp_path / "none.json").encode(), ctypes.byref(n)) == 1
     assert lib.sg_tuning_clear() == 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_run_aware_chunks_random_shapes(seed):
+    # random single-integral shapes and warp counts (from one warp on one SM
+    # up to 8 x 8 per SM): the budget search and the cut runs keep every
+    # table access in its block, visit every pair once, stay within the
+    # resident warps and give the oracle's value
+    rng = np.random.default_rng(1000 + seed)
+    kind = int(rng.choice([1, 2, 4]))
+    fam = int(rng.integers(0, 5))
+    d = int(rng.integers(2, 41))
+    L = int(rng.integers(1, 6 if d < 20 else 4))
+    ctas, warps = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+    case = dict(name="rnd%d" % seed, rule=kind, fam=fam, d=d, L=L, params=si.item_params(fam, d, 77 + seed))
+    for form in (2, 4):
+        r = index_check.run(kind, fam, case["params"], d, L, form=form, ppc=1 << 20, ctas_per_sm=ctas, warps=warps)
+        assert r["violations"] == 0 and r["badpairs"] == 0
+        assert r["evals"] == r["plan_evals"]
+        assert r["chunks"] <= 152 * ctas * warps  # (fewer patterns than warps here)
+        assert _oracle_rel(case, r) < 1e-11
